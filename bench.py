@@ -1,0 +1,312 @@
+"""Benchmark: cell-updates per second per SSP-RK3 stage (FP64) of the TENO-M Euler solver.
+
+Default workload: 2D Euler, 2048 x 2048 periodic, seeded broadband field with four
+circular density/pressure jumps, TENO6-MP, CFL 0.4 (the paper's 2D-shaped workload).
+One step = one SSP-RK3 step (3 stages: CFL reduction, face sweeps on both axes, flux
+difference + stage combine), all on the GPU through the C ABI.
+
+Prints one JSON line.  --impl reference times the CPU oracle (the deliberately slow,
+plain FP64 restatement of the method) on a bounded sample of the same workload.
+Multi-GPU (torchrun): independent replicas, one problem per rank (the method has no
+exchange between problems); value = all ranks' cell updates / max rank time.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (generator, shape x-first, K, limiter)
+    "broadband_2d_2048_teno6_mp": ("broadband_2d", (2048, 2048), 6, 0),
+    "broadband_2d_2048_teno8_tvd5": ("broadband_2d", (2048, 2048), 8, 1),
+    "solenoidal_3d_256_teno8_mp": ("solenoidal_3d", (256, 256, 256), 8, 0),
+}
+DEFAULT = "broadband_2d_2048_teno6_mp"
+FP64_NOMINAL = 1.25e12  # FLOP/s, GB300 FP64 (an FMA counts 2)
+
+
+def flops_per_face(name):
+    """Stored algorithmic FP64 operation counts per face (oracle op counter)."""
+    key = {"broadband_2d_2048_teno6_mp": ("broadband_2d_2048", "K=6", "lim=MP"),
+           "broadband_2d_2048_teno8_tvd5": ("broadband_2d_2048", "K=8", "lim=TVD5"),
+           "solenoidal_3d_256_teno8_mp": ("solenoidal_3d_256", "K=8", "lim=MP")}[name]
+    with open(os.path.join(ROOT, "tests", "golden", "flops_per_face.txt")) as fh:
+        for line in fh:
+            parts = line.split()
+            if parts and not line.startswith("#") and tuple(parts[:3]) == key:
+                vals = [float(x) for x in parts[3:]]
+                return sum(vals) / len(vals)
+    raise KeyError(name)
+
+
+def make_prim(name, seed):
+    from paper_2010_13289_gb300 import problems as PB
+    gen, shape, K, lim = WORKLOADS[name]
+    if gen == "broadband_2d":
+        prim, dx = PB.broadband_2d(shape[0], seed)
+        return prim, (dx, dx)
+    prim, dx = PB.solenoidal_3d(shape[0], seed)
+    return prim, (dx, dx, dx)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+_PRIM_CACHE = {}
+
+
+def cached_prim(name, seed):
+    if (name, seed) not in _PRIM_CACHE:
+        _PRIM_CACHE[(name, seed)] = make_prim(name, seed)
+    return _PRIM_CACHE[(name, seed)]
+
+
+def oracle_rate(name, seconds=12.0, seed=2):
+    """CPU oracle (single thread): one operator evaluation (all axes) on a row block of the
+    workload's initial state, sized for about `seconds` of work.
+    Returns (cell-updates/s per stage, sample description, elapsed s)."""
+    import numpy as np
+    import oracle as orc
+    gen, shape, K, lim = WORKLOADS[name]
+    prim, dx = cached_prim(name, seed)
+    S = orc.make_scheme(K, limiter=lim)
+
+    def block(rows):
+        if len(shape) == 2:
+            p = np.ascontiguousarray(prim[:, :rows, :])
+            sh = (shape[0], rows)
+        else:
+            p = np.ascontiguousarray(prim[:, :rows, :, :])
+            sh = (shape[0], shape[1], rows)
+        g = orc.make_grid(sh, dx, (orc.BC_PERIODIC,) * len(shape))
+        return g, orc.init_state(g, p), int(np.prod(sh))
+    g, U, nc = block(4)
+    t0 = time.perf_counter()
+    orc.rhs(g, S, U)
+    t_cell = (time.perf_counter() - t0) / nc
+    rows = max(4, min(shape[-1], int(seconds / (t_cell * nc / 4))))
+    g, U, nc = block(rows)
+    t0 = time.perf_counter()
+    orc.rhs(g, S, U)
+    el = time.perf_counter() - t0
+    sample = ("one operator evaluation (all %d axes, periodic wrap of the block) on a %s block of the "
+              "%s initial state, 1 thread" % (len(shape), "x".join(str(n) for n in (shape[:-1] + (rows,))), name))
+    return nc / el, sample, el
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    name = args.workload
+    per_step = args.ref_seconds if args.ref_seconds else max(1.0, min(12.0, 150.0 / (args.steps + args.warmup)))
+    rates, samples, times = [], None, []
+    for _ in range(args.warmup):
+        oracle_rate(name, seconds=min(1.0, per_step))
+    for _ in range(args.steps):
+        r, samples, el = oracle_rate(name, seconds=per_step)
+        rates.append(r)
+        times.append(el)
+    v = statistics.median(rates)
+    gen, shape, K, lim = WORKLOADS[name]
+    out = {"impl": "reference", "metric": "cell-updates/s per RK stage (FP64)", "value": v,
+           "unit": "cell-updates/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded, shaped like the paper's workloads)",
+           "config": {"workload": name, "shape": list(shape), "K": K, "limiter": "MP" if lim == 0 else "TVD5"},
+           "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle", "sample": samples},
+           "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2010_13289_gb300 import tenom as T
+
+    name = args.workload
+    gen, shape, K, lim = WORKLOADS[name]
+    prim, dx = make_prim(name, args.seed + rank)
+    S = T.Solver(shape, dx, (T.BC_PERIODIC,) * len(shape), T.make_scheme(K, limiter=lim))
+    U0 = S.init_state(torch.from_numpy(prim).cuda())
+    U = U0.clone()
+    ncell = int(np.prod(shape))
+    nface = sum(ncell // shape[a] * (shape[a] + 1) for a in range(len(shape)))
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up
+    S.advance(U, args.warmup)
+    barrier()
+    # timed region: K SSP-RK3 steps, device-side dt; face kernels timed with events
+    clocks = ClockSampler(local)
+    clocks.start()
+    S.kernel_timing(True)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    S.advance(U, args.steps)
+    ev1.record(stream)
+    barrier()
+    face_ms, face_launches = S.kernel_timing(False)
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = t.item()
+    assert S.status() == 0, "non-physical state in the benchmark run"
+    updates = float(ncell) * 3 * args.steps * ws
+    value = updates / (ms * 1e-3)
+
+    # end to end through the C ABI with host buffers: H2D of the state, one RK3 step, D2H
+    host_in = torch.empty(S.state_shape, dtype=torch.float64, pin_memory=True)
+    host_out = torch.empty(S.state_shape, dtype=torch.float64, pin_memory=True)
+    host_in.copy_(U.cpu())
+    e2e_steps = max(1, min(args.steps, 5))
+    S.advance_host(host_in, host_out, nsteps=1)  # warm
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        S.advance_host(host_in, host_out, nsteps=1)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if ws > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = t.item()
+    e2e = float(ncell) * 3 * e2e_steps * ws / e2e_s
+    state_bytes = 8 * S.nv * ncell
+
+    # roofline of the dominant kernel (face flux): FP64-ALU bound
+    fpf = flops_per_face(name)
+    faces_per_launch = nface / len(shape)
+    achieved = fpf * faces_per_launch / (face_ms * 1e-3) if face_ms > 0 else None
+    probe = T.fp64_peak()
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL, "unit": "FLOP/s",
+            "frac": achieved / FP64_NOMINAL if achieved else None, "traffic": None,
+            "kernel": "face_kernel (fused characteristic TENO-M face flux)",
+            "flops_per_face": fpf, "faces_per_launch": faces_per_launch, "ms_per_launch": face_ms,
+            "launches_timed": face_launches, "peak_note": "nominal GB300 FP64 (FMA = 2 flops)",
+            "fp64_probe_flops": probe}
+    launches_per_step = 3 + 3 * (len(shape) + 1)
+
+    out = {"metric": "cell-updates/s per RK stage (FP64)", "value": value, "unit": "cell-updates/s",
+           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded, shaped like the paper's workloads)",
+           "config": {"workload": name, "shape": list(shape), "K": K, "limiter": "MP" if lim == 0 else "TVD5",
+                      "parallelism": "replicas" if ws > 1 else "single", "cfl": 0.4,
+                      "l2": "working set per stage (state, stage buffer, face buffers: %.0f MB) > L2"
+                            % ((2 * S.nv * ncell + S.nv * nface) * 8 / 1e6)},
+           "e2e": {"value": e2e, "unit": "cell-updates/s", "h2d_bytes_per_step": state_bytes,
+                   "d2h_bytes_per_step": state_bytes},
+           "gpu_launches": launches_per_step * args.steps,
+           "roofline": roof, "clocks": clk}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        r, sample, el = oracle_rate(name, seconds=args.ref_seconds or 12.0, seed=args.seed)
+        out["cpu_baseline"] = {"value": r, "unit": "cell-updates/s", "cores": 1, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    S.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--ref-seconds", type=float, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,149 @@
+/* tenom.h - C ABI of the GB300 (sm_103a) TENO-M library.
+ *
+ * Method: Li, Fu & Adams, "A low-dissipation shock-capturing framework with flexible
+ * nonlinear dissipation control" (arXiv 2010.13289).  The library advances the
+ * compressible Euler equations of an ideal gas on a uniform Cartesian grid
+ * (Section 2, Eqs. conservationlaw-approximateEq, extended dimension by dimension as in
+ * Section 4) with the conservative finite-difference form
+ *     dU_i/dt = - sum_a (Fhat_{a,i+1/2} - Fhat_{a,i-1/2}) / dx_a ,
+ * where every face flux Fhat is built by Roe-averaged characteristic decomposition,
+ * local Lax-Friedrichs (Rusanov) splitting (Section 4), and, per characteristic field and
+ * split side, the TENO-M reconstruction (Sections 2-3: Table 1 candidates, Eqs.
+ * measureTENO/taukTENO indicators, Eqs. normalize/cut-off, Eq. mp_flux filtering of the
+ * nonsmooth candidates by the MP or TVD5 limiter, Eq. reconstuction with w_k = d_k).
+ * Time integration is the third-order SSP Runge-Kutta method (Section 4, CFL 0.4).
+ *
+ * Conventions for every entry point
+ *   - All floating point is IEEE binary64 (double).
+ *   - Grid arrays are caller-owned DEVICE pointers (any allocator, e.g. PyTorch), laid out
+ *     structure-of-arrays [nvar][nz][ny][nx], x fastest, contiguous, 8-byte aligned, no
+ *     ghost cells (boundary conditions are applied inside the library).  nvar = dim + 2:
+ *     (rho, rho*u_1 .. rho*u_dim, E).  Unused trailing extents must be 1.
+ *   - Face arrays of axis a have n_a + 1 entries along a (face f lies between cells f-1
+ *     and f); same ordering otherwise.
+ *   - Calls are asynchronous and ordered on the context's CUDA stream, unless stated.
+ *   - Every call returns tenom_status; nothing aborts or throws across the ABI.  A CUDA
+ *     error is returned as TENOM_E_CUDA; tenom_last_error(ctx) gives the text.
+ *   - Non-physical states met by a kernel (rho <= 0, p <= 0, Roe c^2 <= 0, non-finite
+ *     indicator) set bits in a sticky device status word; tenom_status_word() reads it.
+ *   - A context may be used by one host thread at a time.
+ */
+#ifndef TENOM_H
+#define TENOM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TENOM_OK = 0,
+  TENOM_E_INVALID = 1,      /* bad argument (null/misaligned pointer, bad size or option) */
+  TENOM_E_CUDA = 2,         /* a CUDA runtime call failed */
+  TENOM_E_NONPHYSICAL = 3,  /* device status word has a non-physical bit set */
+  TENOM_E_TIMEOUT = 4,      /* a bounded device wait gave up */
+  TENOM_E_UNSUPPORTED = 5   /* option combination not built */
+} tenom_status;
+
+enum { TENOM_BC_PERIODIC = 0, TENOM_BC_TRANSMISSIVE = 1 };     /* ghost fill: wrap / zero-gradient copy */
+enum { TENOM_LIM_MP = 0, TENOM_LIM_TVD5 = 1, TENOM_LIM_VA = 2 };  /* Section 3.2 limiters */
+enum { TENOM_CT_CONST = 0, TENOM_CT_ADAPTIVE = 1 };            /* C_T fixed, or TENO8A (Section 2.4) */
+enum { TENOM_CURV_M4 = 0, TENOM_CURV_MM = 1 };                 /* MP curvature d_{i+1/2} (Section 3.2.2 / 4) */
+enum { TENOM_W_TENOM = 0, TENOM_W_TENO = 1 };                  /* w_k = d_k (Sec. 3.3) / renormalised (Eq. weight_renormalize) */
+
+/* Device status word bits */
+enum { TENOM_ST_RHO = 1, TENOM_ST_P = 2, TENOM_ST_ROE = 4, TENOM_ST_NONFINITE = 8 };
+
+/* Uniform Cartesian grid of the Euler initial-value problem (Section 2, Section 4). */
+typedef struct tenom_grid {
+  int dim;         /* 1, 2 or 3 */
+  int n[3];        /* cells per axis (x, y, z); unused axes = 1 */
+  double dx[3];    /* spacing per axis; unused axes ignored */
+  int bc[3];       /* TENOM_BC_* per axis */
+  double gamma;    /* ratio of specific heats */
+} tenom_grid;
+
+/* Reconstruction scheme.  Defaults (tenom_scheme_default): K = 6, MP, C_T = 1e-5 constant
+ * (K = 8: adaptive C_T of TENO8A), mp_alpha = 1.25 (Eq. upper_limiter), mp_beta = 4
+ * (Eq. large_curvature), M4 curvature (Eq. maximal_curvature), w_k = d_k with the
+ * maximal-order d_k (Section 3.3 leaves the choice open). */
+typedef struct tenom_scheme {
+  int K;            /* 6 or 8 (Eq. rdistribution: candidates S_0..S_{K-3}) */
+  int limiter;      /* TENOM_LIM_* */
+  int ct_mode;      /* TENOM_CT_* */
+  double ct_const;  /* C_T when ct_mode == TENOM_CT_CONST */
+  double mp_alpha;
+  double mp_beta;
+  int mp_curv;      /* TENOM_CURV_* */
+  int weights;      /* TENOM_W_* */
+  double d[6];      /* optimal weights d_0..d_{K-3}; all zero = maximal-order default */
+} tenom_scheme;
+
+typedef struct tenom_ctx tenom_ctx;
+
+/* Fill *s with the defaults for K (6 or 8).  Host only. */
+tenom_status tenom_scheme_default(tenom_scheme* s, int K);
+
+/* Create a context for one grid and scheme.  stream: a cudaStream_t (NULL = legacy
+ * default stream) on which every call of this context is ordered.  Allocates the
+ * context's device workspace (stage buffer, face buffers, scalars) on the current device:
+ * about (nvar * ncell * (1 + dim) + small) * 8 bytes.  On success *ctx owns it. */
+tenom_status tenom_create(tenom_ctx** ctx, const tenom_grid* grid, const tenom_scheme* scheme, void* stream);
+
+/* Free the context and its workspace (synchronises its stream first).  NULL is a no-op. */
+tenom_status tenom_destroy(tenom_ctx* ctx);
+
+/* Conserved state from primitives (rho, u_1..u_dim, p): U = (rho, rho u, p/(gamma-1) + rho|u|^2/2).
+ * prim and U: device [nvar][ncell].  prim may not alias U. */
+tenom_status tenom_init_state(tenom_ctx* ctx, const double* prim, double* U);
+
+/* Semi-discrete operator dUdt = L(U) = - sum_a (Fhat_{a,i+1/2} - Fhat_{a,i-1/2})/dx_a
+ * (Eq. approximateEq).  U, dUdt: device [nvar][ncell]; dUdt may not alias U. */
+tenom_status tenom_rhs(tenom_ctx* ctx, const double* U, double* dUdt);
+
+/* Stable step dt = cfl / max_i sum_a (|u_a| + c)_i / dx_a (Section 4), written to the
+ * device double *dt_dev (no host synchronisation). */
+tenom_status tenom_max_dt(tenom_ctx* ctx, const double* U, double cfl, double* dt_dev);
+
+/* One SSP-RK3 step in place (Section 4): U1 = U + dt L(U); U2 = 3/4 U + 1/4 (U1 + dt L(U1));
+ * U <- 1/3 U + 2/3 (U2 + dt L(U2)).  dt read from the device double *dt_dev. */
+tenom_status tenom_rk3_step(tenom_ctx* ctx, double* U, const double* dt_dev);
+
+/* nsteps SSP-RK3 steps with dt = min(cfl/max signal speed, t_end - t) recomputed on the
+ * device before each step; t is a device double advanced in place (steps after t reaches
+ * t_end do nothing).  Pass t_end = +inf for unclipped steps. */
+tenom_status tenom_advance(tenom_ctx* ctx, double* U, double* t_dev, double t_end, double cfl, int nsteps);
+
+/* Host-buffer convenience: copy U_host (pinned or pageable, [nvar][ncell]) to the device,
+ * run tenom_advance from t = *t_host, copy the state and t back, synchronise. */
+tenom_status tenom_advance_host(tenom_ctx* ctx, const double* U_host_in, double* U_host_out, double* t_host,
+                                double t_end, double cfl, int nsteps);
+
+/* Diagnostic face dump of axis a for parity checks: the same kernel as the solver writes
+ * Fhat (device [nvar][nface_a]) and per face, field s and split side (0: f+, 1: f-) one
+ * byte flags (device [nface_a][nvar][2]): bits 0..K-3 = delta_k of Eq. cut-off, bits 6-7 =
+ * [beta] - 7 of Eq. cut-off_adjust when C_T is adaptive.  flags may be NULL. */
+tenom_status tenom_face_dump(tenom_ctx* ctx, const double* U, int axis, double* Fhat, uint8_t* flags);
+
+/* Sticky device status word (TENOM_ST_* bits); synchronises the stream.  reset != 0 clears it. */
+tenom_status tenom_status_word(tenom_ctx* ctx, int* status_host, int reset);
+
+/* Text of the last error of this context ("" if none).  Valid until the next call. */
+const char* tenom_last_error(const tenom_ctx* ctx);
+
+/* Measurement helper (not part of the method): average duration in ms of the face kernel
+ * of axis a over the last tenom_rk3_step/tenom_advance calls, timed with CUDA events on
+ * the context stream when timing is enabled.  enable != 0 turns timing on and resets. */
+tenom_status tenom_kernel_timing(tenom_ctx* ctx, int enable, double* face_ms_per_launch, long long* launches);
+
+/* FP64 pipe throughput probe (not part of the method): runs `iters` dependent-chain DFMA
+ * iterations per thread on a grid of nblocks x 256 threads and writes the achieved
+ * FLOP/s (2 per DFMA) to *flops.  Synchronises the stream. */
+tenom_status tenom_fp64_peak(void* stream, int nblocks, int iters, double* flops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TENOM_H */

@@ -112,6 +112,8 @@ def lib():
         L.orc_rk3_step_jvp.restype = c_int
         L.orc_face_flops.argtypes = [gp, sp, dp, c_int]
         L.orc_face_flops.restype = ctypes.c_longlong
+        L.orc_face_flops_at.argtypes = [gp, sp, dp, c_int, ip, c_int]
+        L.orc_face_flops_at.restype = ctypes.c_longlong
         L.orc_roe_eigen.argtypes = [gp, dp, dp, c_int, dp, dp]
         L.orc_phys_flux.argtypes = [gp, dp, c_int, dp]
         L.orc_scalar_rhs.argtypes = [sp, c_int, c_double, dp, dp]
@@ -249,6 +251,13 @@ def rk3_step_jvp(grid, scheme, U, dU, dt):
 
 def face_flops(grid, scheme, U, axis):
     return int(lib().orc_face_flops(ctypes.byref(grid), ctypes.byref(scheme), _d(_c(U)), axis))
+
+
+def face_flops_at(grid, scheme, U, axis, idx):
+    """Counted FP64 operations summed over the faces idx[n, 3]."""
+    idx = _c(idx, np.int32)
+    return int(lib().orc_face_flops_at(ctypes.byref(grid), ctypes.byref(scheme), _d(_c(U)), axis,
+                                       idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), idx.shape[0]))
 
 
 def roe_eigen(grid, UL, UR, axis):

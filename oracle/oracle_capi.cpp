@@ -164,6 +164,22 @@ long long orc_face_flops(const Grid* g, const Scheme* s, const double* U, int ax
   return g_flops;
 }
 
+/* Counted FP64 operations of the faces listed in faces[n][3] (one face per entry). */
+long long orc_face_flops_at(const Grid* g, const Scheme* s, const double* U, int axis, const int* faces, int n) {
+  Grid G = norm_grid(g);
+  Scheme S = norm_scheme(s);
+  long long N = (G.dim + 2) * ncell(G);
+  std::vector<Counted> X(N);
+  for (long long q = 0; q < N; ++q) X[q] = Counted(U[q]);
+  g_flops = 0;
+  for (int q = 0; q < n; ++q) {
+    int idx[3] = {faces[3 * q], faces[3 * q + 1], faces[3 * q + 2]};
+    Counted F[5];
+    face_flux<Counted>(G, S, X.data(), axis, idx, idx[axis], F, nullptr);
+  }
+  return g_flops;
+}
+
 void orc_roe_eigen(const Grid* g, const double* UL, const double* UR, int axis, double* R, double* L) {
   Grid G = norm_grid(g);
   Point<double> PL, PR;

@@ -1,0 +1,590 @@
+/* Host side of the C ABI declared in include/tenom.h, plus the element-wise kernels:
+ * primitive -> conserved state, cell update (flux difference + SSP-RK3 stage combine),
+ * CFL reduction and the FP64 throughput probe.  The face kernels live in
+ * tenom_face_nv{3,4,5}.cu. */
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tenom.h"
+#include "tenom_internal.h"
+
+namespace tenom {
+
+/* ---------------------------------------------------------------- kernels */
+
+/* U = (rho, rho u, p/(gamma-1) + rho|u|^2/2) from (rho, u, p). */
+template <int NV>
+__global__ void init_state_kernel(const double* __restrict__ prim, double* __restrict__ U, long long nc,
+                                  double gamma) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
+    const double rho = prim[c];
+    double ke = 0.0;
+#pragma unroll
+    for (int d = 0; d < NV - 2; ++d) {
+      const double u = prim[(1 + d) * nc + c];
+      U[(1 + d) * nc + c] = rho * u;
+      ke += rho * u * u;
+    }
+    U[c] = rho;
+    U[(NV - 1) * nc + c] = prim[(NV - 1) * nc + c] / (gamma - 1.0) + 0.5 * ke;
+  }
+}
+
+struct StageArgs {
+  const double* F[3];  /* face buffers per axis [NV][nface_a] */
+  const double* U0;    /* U^n (stages 2, 3) */
+  const double* Us;    /* stage input state */
+  double* out;         /* stage output or dU/dt */
+  const double* dt;    /* device dt (null for rhs) */
+  const double* t;     /* device time: steps at t >= t_end are skipped */
+  int n[3];
+  double dx[3];
+  long long ncell;
+  long long nface[3];
+  double cA, cB;       /* out = cA U0 + cB (Us + dt L); cA = 0, cB = 1 for stage 1 */
+  int mode;            /* 0: rhs, 1: stage 1, 2: stages 2/3 */
+  double t_end;
+};
+
+/* Flux difference -sum_a (F_{a,i+1/2} - F_{a,i-1/2})/dx_a (Eq. approximateEq) fused with
+   the SSP-RK3 stage combine. */
+template <int NV>
+__global__ void stage_kernel(const StageArgs A) {
+  constexpr int DIM = NV - 2;
+  const long long nc = A.ncell;
+  double dt = 0.0;
+  if (A.mode != 0) {
+    dt = *A.dt;
+  }
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(c % A.n[0]);
+    const long long yz = c / A.n[0];
+    const int y = (int)(yz % A.n[1]);
+    const int z = (int)(yz / A.n[1]);
+    long long fl[3], fs[3];
+    fl[0] = x + (long long)(A.n[0] + 1) * yz;
+    fs[0] = 1;
+    if (DIM > 1) {
+      fl[1] = x + (long long)A.n[0] * (y + (long long)(A.n[1] + 1) * z);
+      fs[1] = A.n[0];
+    }
+    if (DIM > 2) {
+      fl[2] = c;
+      fs[2] = (long long)A.n[0] * A.n[1];
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      double r = 0.0;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const double* F = A.F[a] + v * A.nface[a];
+        r = r - (F[fl[a] + fs[a]] - F[fl[a]]) / A.dx[a];
+      }
+      if (A.mode == 0) {
+        A.out[v * nc + c] = r;
+      } else if (dt == 0.0) {
+        /* a step past t_end: every stage state equals U^n, keep it bit for bit */
+        A.out[v * nc + c] = A.Us[v * nc + c];
+      } else {
+        const double us = A.Us[v * nc + c];
+        const double t1 = us + dt * r;
+        A.out[v * nc + c] = (A.mode == 1) ? t1 : A.cA * A.U0[v * nc + c] + A.cB * t1;
+      }
+    }
+  }
+}
+
+/* max_i sum_a (|u_a| + c)/dx_a, reduced with atomicMax on the (positive) bit pattern. */
+template <int NV>
+__global__ void signal_speed_kernel(const double* __restrict__ U, long long nc, double gamma, double dx0,
+                                    double dx1, double dx2, unsigned long long* smax, int* status) {
+  constexpr int DIM = NV - 2;
+  const double dx[3] = {dx0, dx1, dx2};
+  double m = 0.0;
+  int st = 0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
+    const double rho = U[c];
+    double vel[DIM], ke = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      vel[d] = U[(1 + d) * nc + c] / rho;
+      ke += U[(1 + d) * nc + c] * vel[d];
+    }
+    const double p = (gamma - 1.0) * (U[(NV - 1) * nc + c] - 0.5 * ke);
+    if (!(rho > 0.0)) st |= ST_RHO;
+    if (!(p > 0.0)) st |= ST_P;
+    const double cs = sqrt(gamma * p / rho);
+    double s = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) s += (fabs(vel[d]) + cs) / dx[d];
+    m = (s > m) ? s : m;
+  }
+  /* warp then block reduction */
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double t = __shfl_xor_sync(0xffffffffu, m, o);
+    m = t > m ? t : m;
+  }
+  __shared__ double red[32];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = m;
+  __syncthreads();
+  if (w == 0) {
+    m = (l < (int)(blockDim.x >> 5)) ? red[l] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double t = __shfl_xor_sync(0xffffffffu, m, o);
+      m = t > m ? t : m;
+    }
+    if (l == 0 && m == m) atomicMax(smax, (unsigned long long)__double_as_longlong(m));
+  }
+  if (st) atomicOr(status, st);
+}
+
+/* dt = min(cfl / smax, t_end - t) (t_end = inf: no clip); resets smax for the next use. */
+__global__ void finalize_dt_kernel(unsigned long long* smax, double cfl, double* dt_out, const double* t,
+                                   double t_end) {
+  const double s = __longlong_as_double((long long)*smax);
+  double dt = cfl / s;
+  if (t) {
+    const double rem = t_end - *t;
+    dt = rem < dt ? rem : dt;
+    if (!(rem > 0.0)) dt = 0.0;
+  }
+  *dt_out = dt;
+  *smax = 0ull;
+}
+
+__global__ void advance_time_kernel(double* t, const double* dt) { *t = *t + *dt; }
+
+/* FP64 pipe probe: 8 independent FMA chains per thread. */
+__global__ void dfma_probe_kernel(int iters, double a, double b, double* sink) {
+  double x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = threadIdx.x * 1e-3 + k;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += x[k];
+  if (s == 12345.678) sink[0] = s;  /* keeps the chains live */
+}
+
+}  // namespace tenom
+
+using namespace tenom;
+
+/* ---------------------------------------------------------------- context */
+
+struct tenom_ctx {
+  tenom_grid g;
+  tenom_scheme s;
+  cudaStream_t st;
+  int nv;
+  long long ncell;
+  long long nface[3];
+  double* W1;          /* stage buffer */
+  double* face[3];     /* face buffers */
+  double* dt;          /* device dt */
+  double* tbuf;        /* device scratch time */
+  double* Uhost;       /* device state for tenom_advance_host (allocated on first use) */
+  unsigned long long* smax;
+  int* status;
+  std::string err;
+  bool timing;
+  std::vector<cudaEvent_t> ev;  /* pairs around face launches */
+  size_t ev_used;
+  double face_ms;
+  long long face_launches;
+};
+
+static tenom_status fail(tenom_ctx* c, tenom_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+static tenom_status cuda_fail(tenom_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, TENOM_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+static SchemeDev scheme_dev(const tenom_scheme& s) {
+  SchemeDev d;
+  memset(&d, 0, sizeof(d));
+  d.ct_mode = s.ct_mode;
+  d.mp_curv = s.mp_curv;
+  d.weights = s.weights;
+  d.ct_const = s.ct_const;
+  d.mp_alpha = s.mp_alpha;
+  d.mp_beta_third = s.mp_beta / 3.0;
+  for (int k = 0; k < 6; ++k) d.d[k] = s.d[k];
+  return d;
+}
+
+static const double kDopt6[4] = {9.0 / 20.0, 3.0 / 10.0, 1.0 / 20.0, 1.0 / 5.0};
+static const double kDopt8[6] = {3.0 / 7.0, 9.0 / 35.0, 2.0 / 35.0, 6.0 / 35.0, 1.0 / 70.0, 1.0 / 14.0};
+
+extern "C" {
+
+tenom_status tenom_scheme_default(tenom_scheme* s, int K) {
+  if (!s || (K != 6 && K != 8)) return TENOM_E_INVALID;
+  memset(s, 0, sizeof(*s));
+  s->K = K;
+  s->limiter = TENOM_LIM_MP;
+  s->ct_mode = (K == 6) ? TENOM_CT_CONST : TENOM_CT_ADAPTIVE;
+  s->ct_const = 1e-5;
+  s->mp_alpha = 1.25;
+  s->mp_beta = 4.0;
+  s->mp_curv = TENOM_CURV_M4;
+  s->weights = TENOM_W_TENOM;
+  for (int k = 0; k < K - 2; ++k) s->d[k] = (K == 6) ? kDopt6[k] : kDopt8[k];
+  return TENOM_OK;
+}
+
+static tenom_status validate(const tenom_grid* g, const tenom_scheme* s, std::string* msg) {
+  if (!g || !s) { *msg = "null grid or scheme"; return TENOM_E_INVALID; }
+  if (g->dim < 1 || g->dim > 3) { *msg = "dim must be 1, 2 or 3"; return TENOM_E_INVALID; }
+  for (int a = 0; a < 3; ++a) {
+    if (a < g->dim) {
+      if (g->n[a] < 1 || g->n[a] > (1 << 24)) { *msg = "cell count out of range"; return TENOM_E_INVALID; }
+      if (!(g->dx[a] > 0.0) || !std::isfinite(g->dx[a])) { *msg = "dx must be positive"; return TENOM_E_INVALID; }
+      if (g->bc[a] != TENOM_BC_PERIODIC && g->bc[a] != TENOM_BC_TRANSMISSIVE) { *msg = "bad bc"; return TENOM_E_INVALID; }
+    } else if (g->n[a] != 1) {
+      *msg = "unused axes must have n = 1";
+      return TENOM_E_INVALID;
+    }
+  }
+  if (!(g->gamma > 1.0)) { *msg = "gamma must exceed 1"; return TENOM_E_INVALID; }
+  long long nc = (long long)g->n[0] * g->n[1] * g->n[2];
+  if (nc > (1ll << 31)) { *msg = "grid too large"; return TENOM_E_INVALID; }
+  if (g->dim > 1 && (long long)g->n[1] * g->n[2] > 2147483647ll) { *msg = "too many rows"; return TENOM_E_INVALID; }
+  if (s->K != 6 && s->K != 8) { *msg = "K must be 6 or 8"; return TENOM_E_INVALID; }
+  if (s->limiter != TENOM_LIM_MP && s->limiter != TENOM_LIM_TVD5) {
+    *msg = "limiter not built (MP and TVD5 are)";
+    return TENOM_E_UNSUPPORTED;
+  }
+  if (s->ct_mode != TENOM_CT_CONST && s->ct_mode != TENOM_CT_ADAPTIVE) { *msg = "bad ct_mode"; return TENOM_E_INVALID; }
+  if (s->mp_curv != TENOM_CURV_M4 && s->mp_curv != TENOM_CURV_MM) { *msg = "bad mp_curv"; return TENOM_E_INVALID; }
+  if (s->weights != TENOM_W_TENOM && s->weights != TENOM_W_TENO) { *msg = "bad weights"; return TENOM_E_INVALID; }
+  for (int a = 0; a < g->dim; ++a)
+    if (g->n[a] < s->K / 2 && g->bc[a] == TENOM_BC_PERIODIC) {
+      *msg = "periodic axis shorter than the half stencil";
+      return TENOM_E_INVALID;
+    }
+  return TENOM_OK;
+}
+
+tenom_status tenom_create(tenom_ctx** out, const tenom_grid* grid, const tenom_scheme* scheme, void* stream) {
+  if (!out) return TENOM_E_INVALID;
+  *out = nullptr;
+  std::string msg;
+  tenom_status v = validate(grid, scheme, &msg);
+  if (v != TENOM_OK) {
+    fprintf(stderr, "tenom_create: %s\n", msg.c_str());
+    return v;
+  }
+  tenom_ctx* c = new tenom_ctx();
+  c->g = *grid;
+  c->s = *scheme;
+  bool anyd = false;
+  for (int k = 0; k < 6; ++k) anyd |= (c->s.d[k] != 0.0);
+  if (!anyd)
+    for (int k = 0; k < c->s.K - 2; ++k) c->s.d[k] = (c->s.K == 6) ? kDopt6[k] : kDopt8[k];
+  c->st = (cudaStream_t)stream;
+  c->nv = grid->dim + 2;
+  c->ncell = (long long)grid->n[0] * grid->n[1] * grid->n[2];
+  for (int a = 0; a < 3; ++a) {
+    c->nface[a] = 0;
+    c->face[a] = nullptr;
+    if (a < grid->dim) c->nface[a] = c->ncell / grid->n[a] * (grid->n[a] + 1);
+  }
+  c->Uhost = nullptr;
+  c->timing = false;
+  c->ev_used = 0;
+  c->face_ms = 0;
+  c->face_launches = 0;
+  cudaError_t e = cudaMalloc(&c->W1, sizeof(double) * c->nv * c->ncell);
+  for (int a = 0; a < grid->dim && e == cudaSuccess; ++a) e = cudaMalloc(&c->face[a], sizeof(double) * c->nv * c->nface[a]);
+  if (e == cudaSuccess) e = cudaMalloc(&c->dt, sizeof(double) * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&c->smax, sizeof(unsigned long long) + sizeof(int) * 2);
+  if (e == cudaSuccess) {
+    c->tbuf = c->dt + 1;
+    c->status = (int*)(c->smax + 1);
+    e = cudaMemsetAsync(c->smax, 0, sizeof(unsigned long long) + sizeof(int) * 2, c->st);
+  }
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->dt, 0, sizeof(double) * 2, c->st);
+  if (e != cudaSuccess) {
+    fprintf(stderr, "tenom_create: %s\n", cudaGetErrorString(e));
+    tenom_destroy(c);
+    return TENOM_E_CUDA;
+  }
+  *out = c;
+  return TENOM_OK;
+}
+
+tenom_status tenom_destroy(tenom_ctx* c) {
+  if (!c) return TENOM_OK;
+  cudaStreamSynchronize(c->st);
+  cudaFree(c->W1);
+  for (int a = 0; a < 3; ++a) cudaFree(c->face[a]);
+  cudaFree(c->dt);
+  cudaFree(c->smax);
+  cudaFree(c->Uhost);
+  for (cudaEvent_t ev : c->ev) cudaEventDestroy(ev);
+  delete c;
+  return TENOM_OK;
+}
+
+const char* tenom_last_error(const tenom_ctx* c) { return c ? c->err.c_str() : ""; }
+
+static bool aligned8(const void* p) { return p && ((uintptr_t)p & 7) == 0; }
+
+static unsigned ew_blocks(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+tenom_status tenom_init_state(tenom_ctx* c, const double* prim, double* U) {
+  if (!c) return TENOM_E_INVALID;
+  if (!aligned8(prim) || !aligned8(U) || prim == U) return fail(c, TENOM_E_INVALID, "init_state: bad pointers");
+  unsigned nb = ew_blocks(c->ncell);
+  if (c->nv == 3) init_state_kernel<3><<<nb, 256, 0, c->st>>>(prim, U, c->ncell, c->g.gamma);
+  else if (c->nv == 4) init_state_kernel<4><<<nb, 256, 0, c->st>>>(prim, U, c->ncell, c->g.gamma);
+  else init_state_kernel<5><<<nb, 256, 0, c->st>>>(prim, U, c->ncell, c->g.gamma);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? TENOM_OK : cuda_fail(c, e, "init_state");
+}
+
+static FaceArgs face_args(tenom_ctx* c, const double* U, int axis, double* F, uint8_t* flags) {
+  FaceArgs a;
+  memset(&a, 0, sizeof(a));
+  a.U = U;
+  a.Fhat = F;
+  a.flags = flags;
+  a.status = c->status;
+  for (int d = 0; d < 3; ++d) {
+    a.n[d] = c->g.n[d];
+    a.bc[d] = c->g.bc[d];
+  }
+  a.ncell = c->ncell;
+  a.nface = c->nface[axis];
+  a.gamma = c->g.gamma;
+  a.sch = scheme_dev(c->s);
+  return a;
+}
+
+static cudaError_t launch_faces(tenom_ctx* c, const double* U, int axis, double* F, uint8_t* flags) {
+  FaceArgs a = face_args(c, U, axis, F, flags);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (c->timing) {
+    while (c->ev.size() < c->ev_used + 2) {
+      cudaEvent_t ev;
+      cudaError_t er = cudaEventCreate(&ev);
+      if (er != cudaSuccess) return er;
+      c->ev.push_back(ev);
+    }
+    e0 = c->ev[c->ev_used];
+    e1 = c->ev[c->ev_used + 1];
+    c->ev_used += 2;
+    cudaEventRecord(e0, c->st);
+  }
+  cudaError_t e;
+  if (c->nv == 3) e = launch_face_nv3(a, axis, c->s.K, c->s.limiter, c->st);
+  else if (c->nv == 4) e = launch_face_nv4(a, axis, c->s.K, c->s.limiter, c->st);
+  else e = launch_face_nv5(a, axis, c->s.K, c->s.limiter, c->st);
+  if (c->timing) cudaEventRecord(e1, c->st);
+  return e;
+}
+
+static cudaError_t launch_stage(tenom_ctx* c, const double* U0, const double* Us, double* out, int mode, double cA,
+                                double cB) {
+  StageArgs a;
+  memset(&a, 0, sizeof(a));
+  for (int d = 0; d < 3; ++d) {
+    a.F[d] = c->face[d];
+    a.n[d] = c->g.n[d];
+    a.dx[d] = c->g.dx[d];
+    a.nface[d] = c->nface[d];
+  }
+  a.U0 = U0;
+  a.Us = Us;
+  a.out = out;
+  a.dt = c->dt;
+  a.ncell = c->ncell;
+  a.cA = cA;
+  a.cB = cB;
+  a.mode = mode;
+  unsigned nb = ew_blocks(c->ncell);
+  if (c->nv == 3) stage_kernel<3><<<nb, 256, 0, c->st>>>(a);
+  else if (c->nv == 4) stage_kernel<4><<<nb, 256, 0, c->st>>>(a);
+  else stage_kernel<5><<<nb, 256, 0, c->st>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t eval_faces(tenom_ctx* c, const double* U) {
+  for (int a = 0; a < c->g.dim; ++a) {
+    cudaError_t e = launch_faces(c, U, a, c->face[a], nullptr);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+tenom_status tenom_rhs(tenom_ctx* c, const double* U, double* dUdt) {
+  if (!c) return TENOM_E_INVALID;
+  if (!aligned8(U) || !aligned8(dUdt) || U == dUdt) return fail(c, TENOM_E_INVALID, "rhs: bad pointers");
+  cudaError_t e = eval_faces(c, U);
+  if (e == cudaSuccess) e = launch_stage(c, nullptr, U, dUdt, 0, 0.0, 0.0);
+  return e == cudaSuccess ? TENOM_OK : cuda_fail(c, e, "rhs");
+}
+
+static cudaError_t launch_signal(tenom_ctx* c, const double* U) {
+  unsigned nb = ew_blocks(c->ncell);
+  const double* dx = c->g.dx;
+  if (c->nv == 3) signal_speed_kernel<3><<<nb, 256, 0, c->st>>>(U, c->ncell, c->g.gamma, dx[0], dx[1], dx[2], c->smax, c->status);
+  else if (c->nv == 4) signal_speed_kernel<4><<<nb, 256, 0, c->st>>>(U, c->ncell, c->g.gamma, dx[0], dx[1], dx[2], c->smax, c->status);
+  else signal_speed_kernel<5><<<nb, 256, 0, c->st>>>(U, c->ncell, c->g.gamma, dx[0], dx[1], dx[2], c->smax, c->status);
+  return cudaGetLastError();
+}
+
+tenom_status tenom_max_dt(tenom_ctx* c, const double* U, double cfl, double* dt_dev) {
+  if (!c) return TENOM_E_INVALID;
+  if (!aligned8(U) || !aligned8(dt_dev) || !(cfl > 0.0)) return fail(c, TENOM_E_INVALID, "max_dt: bad arguments");
+  cudaError_t e = launch_signal(c, U);
+  if (e == cudaSuccess) {
+    finalize_dt_kernel<<<1, 1, 0, c->st>>>(c->smax, cfl, dt_dev, nullptr, 0.0);
+    e = cudaGetLastError();
+  }
+  return e == cudaSuccess ? TENOM_OK : cuda_fail(c, e, "max_dt");
+}
+
+/* three stages; dt already in c->dt */
+static cudaError_t rk3_core(tenom_ctx* c, double* U) {
+  cudaError_t e = eval_faces(c, U);
+  if (e == cudaSuccess) e = launch_stage(c, nullptr, U, c->W1, 1, 0.0, 1.0);
+  if (e == cudaSuccess) e = eval_faces(c, c->W1);
+  if (e == cudaSuccess) e = launch_stage(c, U, c->W1, c->W1, 2, 0.75, 0.25);
+  if (e == cudaSuccess) e = eval_faces(c, c->W1);
+  if (e == cudaSuccess) e = launch_stage(c, U, c->W1, U, 2, 1.0 / 3.0, 2.0 / 3.0);
+  return e;
+}
+
+tenom_status tenom_rk3_step(tenom_ctx* c, double* U, const double* dt_dev) {
+  if (!c) return TENOM_E_INVALID;
+  if (!aligned8(U) || !aligned8(dt_dev)) return fail(c, TENOM_E_INVALID, "rk3_step: bad pointers");
+  cudaError_t e = cudaSuccess;
+  if (dt_dev != c->dt) e = cudaMemcpyAsync(c->dt, dt_dev, sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+  if (e == cudaSuccess) e = rk3_core(c, U);
+  return e == cudaSuccess ? TENOM_OK : cuda_fail(c, e, "rk3_step");
+}
+
+tenom_status tenom_advance(tenom_ctx* c, double* U, double* t_dev, double t_end, double cfl, int nsteps) {
+  if (!c) return TENOM_E_INVALID;
+  if (!aligned8(U) || !aligned8(t_dev) || !(cfl > 0.0) || nsteps < 0 || !(t_end == t_end))
+    return fail(c, TENOM_E_INVALID, "advance: bad arguments");
+  for (int k = 0; k < nsteps; ++k) {
+    cudaError_t e = launch_signal(c, U);
+    if (e == cudaSuccess) {
+      finalize_dt_kernel<<<1, 1, 0, c->st>>>(c->smax, cfl, c->dt, t_dev, t_end);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = rk3_core(c, U);
+    if (e == cudaSuccess) {
+      advance_time_kernel<<<1, 1, 0, c->st>>>(t_dev, c->dt);
+      e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "advance");
+  }
+  return TENOM_OK;
+}
+
+tenom_status tenom_advance_host(tenom_ctx* c, const double* U_in, double* U_out, double* t_host, double t_end,
+                                double cfl, int nsteps) {
+  if (!c) return TENOM_E_INVALID;
+  if (!U_in || !U_out || !t_host) return fail(c, TENOM_E_INVALID, "advance_host: null pointer");
+  size_t bytes = sizeof(double) * c->nv * c->ncell;
+  cudaError_t e = cudaSuccess;
+  if (!c->Uhost) e = cudaMalloc(&c->Uhost, bytes);
+  double* Ud = c->Uhost;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(Ud, U_in, bytes, cudaMemcpyHostToDevice, c->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->tbuf, t_host, sizeof(double), cudaMemcpyHostToDevice, c->st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "advance_host");
+  tenom_status s = tenom_advance(c, Ud, c->tbuf, t_end, cfl, nsteps);
+  if (s == TENOM_OK) {
+    e = cudaMemcpyAsync(U_out, Ud, bytes, cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(t_host, c->tbuf, sizeof(double), cudaMemcpyDeviceToHost, c->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "advance_host");
+  }
+  return s;
+}
+
+tenom_status tenom_face_dump(tenom_ctx* c, const double* U, int axis, double* Fhat, uint8_t* flags) {
+  if (!c) return TENOM_E_INVALID;
+  if (axis < 0 || axis >= c->g.dim) return fail(c, TENOM_E_INVALID, "face_dump: bad axis");
+  if (!aligned8(U) || !aligned8(Fhat)) return fail(c, TENOM_E_INVALID, "face_dump: bad pointers");
+  bool t = c->timing;
+  c->timing = false;
+  cudaError_t e = launch_faces(c, U, axis, Fhat, flags);
+  c->timing = t;
+  return e == cudaSuccess ? TENOM_OK : cuda_fail(c, e, "face_dump");
+}
+
+tenom_status tenom_status_word(tenom_ctx* c, int* status_host, int reset) {
+  if (!c || !status_host) return TENOM_E_INVALID;
+  cudaError_t e = cudaMemcpyAsync(status_host, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+  if (e == cudaSuccess && reset) e = cudaMemsetAsync(c->status, 0, sizeof(int), c->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "status_word");
+  return *status_host ? TENOM_E_NONPHYSICAL : TENOM_OK;
+}
+
+tenom_status tenom_kernel_timing(tenom_ctx* c, int enable, double* face_ms_per_launch, long long* launches) {
+  if (!c) return TENOM_E_INVALID;
+  cudaError_t e = cudaStreamSynchronize(c->st);
+  if (e != cudaSuccess) return cuda_fail(c, e, "kernel_timing");
+  double tot = 0.0;
+  long long n = 0;
+  for (size_t k = 0; k + 1 < c->ev_used; k += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[k], c->ev[k + 1]) == cudaSuccess) {
+      tot += ms;
+      ++n;
+    }
+  }
+  if (face_ms_per_launch) *face_ms_per_launch = n ? tot / n : 0.0;
+  if (launches) *launches = n;
+  c->ev_used = 0;
+  c->timing = enable != 0;
+  return TENOM_OK;
+}
+
+tenom_status tenom_fp64_peak(void* stream, int nblocks, int iters, double* flops) {
+  if (nblocks < 1 || iters < 1 || !flops) return TENOM_E_INVALID;
+  cudaStream_t st = (cudaStream_t)stream;
+  double* sink = nullptr;
+  cudaEvent_t a, b;
+  cudaError_t e = cudaMalloc(&sink, sizeof(double));
+  if (e != cudaSuccess) return TENOM_E_CUDA;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  dfma_probe_kernel<<<nblocks, 256, 0, st>>>(iters / 8 + 1, 0.999999, 1e-7, sink);  /* warm-up */
+  cudaEventRecord(a, st);
+  dfma_probe_kernel<<<nblocks, 256, 0, st>>>(iters, 0.999999, 1e-7, sink);
+  cudaEventRecord(b, st);
+  e = cudaEventSynchronize(b);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, a, b);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  cudaFree(sink);
+  if (e != cudaSuccess) return TENOM_E_CUDA;
+  *flops = 2.0 * 8.0 * (double)iters * nblocks * 256.0 / (ms * 1e-3);
+  return TENOM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,253 @@
+/* Fused characteristic face-flux kernel (Section 4 of arXiv 2010.13289: Roe-averaged
+ * characteristic decomposition, Rusanov / local Lax-Friedrichs splitting, TENO-M per
+ * characteristic field and split side, back-projection).
+ *
+ * One CTA owns a tile of consecutive faces along the sweep axis:
+ *   axis x : 128 faces of one row, one thread per face (x is contiguous);
+ *   axis y,z: 32 contiguous x-columns (lanes) x FT faces along the axis (warps).
+ * Phase 1 stages the tile's points (faces + K-1 halo points, boundary condition applied
+ * at load: periodic wrap or zero-gradient clamp) and computes every point quantity once
+ * into shared memory: U, the physical flux F_a(U), velocity, total enthalpy H, sound
+ * speed c and sqrt(rho).  Phase 2 computes each face flux exactly once and writes it to
+ * the face buffer [nvar][nface_a]; the cell update (flux difference) reads it later, so
+ * both neighbouring cells use the same face value.
+ */
+#pragma once
+#include <cstdint>
+#include "tenom_recon.cuh"
+
+namespace tenom {
+
+struct FaceArgs {
+  const double* U;    /* [NV][ncell] */
+  double* Fhat;       /* [NV][nface] */
+  uint8_t* flags;     /* [nface][NV][2] or null */
+  int* status;        /* sticky status word */
+  int n[3];
+  int bc[3];
+  long long ncell;
+  long long nface;
+  double gamma;
+  SchemeDev sch;
+};
+
+constexpr int FX_FACES = 128;  /* faces per CTA, x sweeps */
+constexpr int FT_FACES = 8;    /* faces per CTA along the axis, y/z sweeps (x 32 lanes) */
+
+template <int NV, int K, int AXIS>
+struct FaceTile {
+  static constexpr int H = K / 2;
+  static constexpr int NC = 3 * NV + 1;  /* U[NV], F[NV], vel[NV-2], H, c, sqrt(rho) */
+  static constexpr int LANES = (AXIS == 0) ? 1 : 32;
+  static constexpr int FACES = (AXIS == 0) ? FX_FACES : FT_FACES;
+  static constexpr int ROWS = FACES + K - 1;     /* points along the axis */
+  static constexpr int NP = ROWS * LANES;        /* points per tile */
+  static constexpr int THREADS = FACES * LANES;
+  static constexpr size_t SMEM = sizeof(double) * NC * NP;
+  /* component offsets */
+  static constexpr int cU = 0, cF = NV, cV = 2 * NV, cH = 3 * NV - 2, cC = 3 * NV - 1, cS = 3 * NV;
+};
+
+__device__ __forceinline__ int bc_wrap(int j, int n, int bc) {
+  if (bc == 0) {
+    j %= n;
+    return j < 0 ? j + n : j;
+  }
+  return j < 0 ? 0 : (j >= n ? n - 1 : j);
+}
+
+template <int NV, int K, int LIM, int AXIS>
+__global__ void __launch_bounds__(FaceTile<NV, K, AXIS>::THREADS)
+face_kernel(const FaceArgs A) {
+  using T = FaceTile<NV, K, AXIS>;
+  constexpr int D = NV - 2;
+  constexpr int H = T::H;
+  extern __shared__ double sm[];
+  const int tid = threadIdx.x;
+
+  /* --- tile coordinates --- */
+  const int na = A.n[AXIS];
+  int f0, x0 = 0, o1 = 0, o2 = 0;
+  if (AXIS == 0) {
+    const int row = blockIdx.x;          /* y + ny * z */
+    o1 = row % A.n[1];
+    o2 = row / A.n[1];
+    f0 = blockIdx.y * T::FACES;
+  } else {
+    x0 = blockIdx.x * 32;
+    f0 = blockIdx.y * T::FACES;
+    o2 = blockIdx.z;                     /* AXIS 1: z ; AXIS 2: y */
+  }
+  const long long sx = 1, sy = A.n[0], sz = (long long)A.n[0] * A.n[1];
+  const long long sa = (AXIS == 0) ? sx : (AXIS == 1 ? sy : sz);
+
+  /* --- phase 1: point quantities --- */
+  int st = 0;
+  for (int p = tid; p < T::NP; p += T::THREADS) {
+    const int lane = (AXIS == 0) ? 0 : (p & 31);
+    const int row = (AXIS == 0) ? p : (p >> 5);
+    const int j = bc_wrap(f0 - H + row, na, A.bc[AXIS]);
+    long long base;
+    if (AXIS == 0) base = sy * o1 + sz * o2;
+    else {
+      int x = x0 + lane;
+      x = x < A.n[0] ? x : A.n[0] - 1;
+      base = x + (AXIS == 1 ? sz * o2 : sy * o2);
+    }
+    const long long cell = base + sa * j;
+    double u[NV];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) u[q] = __ldg(A.U + q * A.ncell + cell);
+    const double rho = u[0];
+    const double rinv = 1.0 / rho;
+    double vel[D], ke = 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      vel[d] = u[1 + d] * rinv;
+      ke += u[1 + d] * vel[d];
+    }
+    const double pr = (A.gamma - 1.0) * (u[NV - 1] - 0.5 * ke);
+    const double c = sqrt(A.gamma * pr * rinv);
+    const double Hh = (u[NV - 1] + pr) * rinv;
+    if (!(rho > 0.0)) st |= ST_RHO;
+    if (!(pr > 0.0)) st |= ST_P;
+    const double un = vel[AXIS];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) sm[(T::cU + q) * T::NP + p] = u[q];
+    sm[(T::cF + 0) * T::NP + p] = u[0] * un;
+#pragma unroll
+    for (int d = 0; d < D; ++d) sm[(T::cF + 1 + d) * T::NP + p] = u[1 + d] * un + (d == AXIS ? pr : 0.0);
+    sm[(T::cF + NV - 1) * T::NP + p] = (u[NV - 1] + pr) * un;
+#pragma unroll
+    for (int d = 0; d < D; ++d) sm[(T::cV + d) * T::NP + p] = vel[d];
+    sm[T::cH * T::NP + p] = Hh;
+    sm[T::cC * T::NP + p] = c;
+    sm[T::cS * T::NP + p] = sqrt(rho);
+  }
+  __syncthreads();
+
+  /* --- phase 2: one face per thread --- */
+  const int lane = (AXIS == 0) ? 0 : (tid & 31);
+  const int jf = (AXIS == 0) ? tid : (tid >> 5);
+  const int f = f0 + jf;
+  const int xg = x0 + lane;
+  bool active = (f <= na) && (AXIS == 0 || xg < A.n[0]);
+  if (active) {
+    auto P = [&](int comp, int q) -> double {
+      return sm[comp * T::NP + (jf + q) * T::LANES + lane];
+    };
+    /* Roe average of cells f-1 (point H-1) and f (point H) */
+    const double sL = P(T::cS, H - 1), sR = P(T::cS, H);
+    const double wsum = 1.0 / (sL + sR);
+    double ut[D], q2 = 0.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      ut[d] = (sL * P(T::cV + d, H - 1) + sR * P(T::cV + d, H)) * wsum;
+      q2 += ut[d] * ut[d];
+    }
+    const double Ht = (sL * P(T::cH, H - 1) + sR * P(T::cH, H)) * wsum;
+    const double c2 = (A.gamma - 1.0) * (Ht - 0.5 * q2);
+    if (!(c2 > 0.0)) st |= ST_ROE;
+    const double ct = sqrt(c2);
+    const double cinv = 1.0 / ct;
+    const double b1 = (A.gamma - 1.0) / c2;
+    const double b2 = 0.5 * q2 * b1;
+    const double una = ut[AXIS];
+
+    double Fh[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Fh[v] = 0.0;
+    /* face linear index (n_a + 1 entries along the axis) */
+    long long flin;
+    if (AXIS == 0) flin = f + (long long)(A.n[0] + 1) * (o1 + (long long)A.n[1] * o2);
+    else if (AXIS == 1) flin = xg + (long long)A.n[0] * (f + (long long)(A.n[1] + 1) * o2);
+    else flin = xg + (long long)A.n[0] * (o2 + (long long)A.n[1] * f);
+
+#pragma unroll 1
+    for (int s = 0; s < NV; ++s) {
+      const bool acoustic = (s == 0) || (s == NV - 1);
+      const double sg = (s == 0) ? 1.0 : -1.0;            /* l: +1 for u-c, -1 for u+c */
+      const int dt = (s - 2) < AXIS ? (s - 2) : (s - 1);  /* shear fields: tangential axes in increasing order */
+      double utt = 0.0;
+#pragma unroll
+      for (int d = 0; d < D; ++d) utt = (d == dt) ? ut[d] : utt;
+      /* left eigenvector l_s (closed form of R^{-1}) */
+      double l[NV];
+      if (acoustic) {
+        l[0] = 0.5 * (b2 + sg * una * cinv);
+#pragma unroll
+        for (int d = 0; d < D; ++d) l[1 + d] = 0.5 * (-b1 * ut[d] - (d == AXIS ? sg * cinv : 0.0));
+        l[NV - 1] = 0.5 * b1;
+      } else if (s == 1) {
+        l[0] = 1.0 - b2;
+#pragma unroll
+        for (int d = 0; d < D; ++d) l[1 + d] = b1 * ut[d];
+        l[NV - 1] = -b1;
+      } else {
+        l[0] = -utt;
+#pragma unroll
+        for (int d = 0; d < D; ++d) l[1 + d] = (d == dt) ? 1.0 : 0.0;
+        l[NV - 1] = 0.0;
+      }
+      /* project the K stencil points; LLF alpha_s = max_m |lambda_s(U_m)| */
+      double gp[K], gm[K];
+      double alpha = 0.0;
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        double w = 0.0, g = 0.0;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          w += l[v] * P(T::cU + v, q);
+          g += l[v] * P(T::cF + v, q);
+        }
+        const double un = P(T::cV + AXIS, q);
+        const double cq = P(T::cC, q);
+        const double lam = (s == 0) ? un - cq : (s == NV - 1 ? un + cq : un);
+        alpha = (q == 0) ? fabs(lam) : dmax(alpha, fabs(lam));
+        gp[q] = w;  /* hold W, G until alpha is known */
+        gm[q] = g;
+      }
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        const double w = gp[q], g = gm[q];
+        gp[q] = 0.5 * (g + alpha * w);
+        gm[q] = 0.5 * (g - alpha * w);
+      }
+      /* f+ on the upwind stencil, f- on the stencil mirrored about x_{i+1/2} */
+      double vm[K];
+#pragma unroll
+      for (int q = 0; q < K; ++q) vm[q] = gm[K - 1 - q];
+      unsigned flp, flm;
+      const double fplus = teno_m<K, LIM>(gp, A.sch, flp, st);
+      const double fminus = teno_m<K, LIM>(vm, A.sch, flm, st);
+      if (A.flags) {
+        A.flags[(flin * NV + s) * 2 + 0] = (uint8_t)flp;
+        A.flags[(flin * NV + s) * 2 + 1] = (uint8_t)flm;
+      }
+      const double fs = fplus + fminus;
+      /* back-projection F += r_s fs */
+      if (acoustic) {
+        const double sr = -sg;                            /* r: -c for u-c, +c for u+c */
+        Fh[0] += fs;
+#pragma unroll
+        for (int d = 0; d < D; ++d) Fh[1 + d] += (ut[d] + (d == AXIS ? sr * ct : 0.0)) * fs;
+        Fh[NV - 1] += (Ht + sr * una * ct) * fs;
+      } else if (s == 1) {
+        Fh[0] += fs;
+#pragma unroll
+        for (int d = 0; d < D; ++d) Fh[1 + d] += ut[d] * fs;
+        Fh[NV - 1] += 0.5 * q2 * fs;
+      } else {
+#pragma unroll
+        for (int d = 0; d < D; ++d)
+          if (d == dt) Fh[1 + d] += fs;
+        Fh[NV - 1] += utt * fs;
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) A.Fhat[v * A.nface + flin] = Fh[v];
+  }
+  if (st) atomicOr(A.status, st);
+}
+
+}  // namespace tenom

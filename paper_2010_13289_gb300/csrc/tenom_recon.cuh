@@ -1,0 +1,199 @@
+/* Scalar TENO-M reconstruction on the device (Sections 2-3 of arXiv 2010.13289).
+ *
+ * Input: K register values v[0..K-1] = f_{i-K/2+1} .. f_{i+K/2}; output the reconstructed
+ * h(x_{i+1/2}).  Steps in the paper's order:
+ *   candidates f_{k,i+1/2} (Table 1),
+ *   indicators beta_{k,r}, beta_K (Eq. measureTENO, 2nd line), tau_K (Eq. taukTENO),
+ *   gamma_k = (1 + tau_K/(beta_k + 1e-40))^6 (Eq. measureTENO, C = 1, q = 6),
+ *   chi_k = gamma_k / sum gamma (Eq. normalize), delta_k = [chi_k >= C_T] (Eq. cut-off),
+ *   C_T constant or adaptive (TENO8A, Eqs. shock_indicator, cut-off_adjust),
+ *   nonsmooth candidates filtered by MP (Eqs. minmod222-value_monotonicity_preserving)
+ *   or replaced by the fixed TVD5 flux (Eqs. high order TVD-TVDbeta) (Eq. mp_flux),
+ *   assembly with constant weights w_k = d_k (Eq. reconstuction, Section 3.3).
+ * The indicators use exact sum-of-squares forms over the differences D_t = v[t+1] - v[t]
+ * (teno_coeffs.cuh); the TVD5 flux is evaluated in its division-free difference form.
+ */
+#pragma once
+#include <cstdint>
+#include "teno_coeffs.cuh"
+
+namespace tenom {
+
+enum { LIM_MP = 0, LIM_TVD5 = 1, LIM_VA = 2 };
+enum { CT_CONST = 0, CT_ADAPTIVE = 1 };
+enum { CURV_M4 = 0, CURV_MM = 1 };
+enum { W_TENOM = 0, W_TENO = 1 };
+enum { ST_RHO = 1, ST_P = 2, ST_ROE = 4, ST_NONFINITE = 8 };
+
+struct SchemeDev {
+  int ct_mode;
+  int mp_curv;
+  int weights;
+  int pad_;
+  double ct_const;
+  double mp_alpha;
+  double mp_beta_third;  /* mp_beta / 3 */
+  double d[6];
+};
+
+__device__ __forceinline__ double dmin(double a, double b) { return b < a ? b : a; }
+__device__ __forceinline__ double dmax(double a, double b) { return a < b ? b : a; }
+
+/* minmod of two arguments (Eq. minmod222; zero if an argument is zero). */
+__device__ __forceinline__ double minmod2(double x, double y) {
+  if (x > 0.0 && y > 0.0) return dmin(x, y);
+  if (x < 0.0 && y < 0.0) return dmax(x, y);
+  return 0.0;
+}
+
+/* minmod of four arguments (Eq. minmod444). */
+__device__ __forceinline__ double minmod4(double a, double b, double c, double d) {
+  if (a > 0.0 && b > 0.0 && c > 0.0 && d > 0.0) return dmin(dmin(a, b), dmin(c, d));
+  if (a < 0.0 && b < 0.0 && c < 0.0 && d < 0.0) return dmax(dmax(a, b), dmax(c, d));
+  return 0.0;
+}
+
+/* median(x, y, z) = x + minmod(y - x, z - x) (Eq. median). */
+__device__ __forceinline__ double median3(double x, double y, double z) { return x + minmod2(y - x, z - x); }
+
+/* MP bounds f^{L,min}, f^{L,max} at x_{i+1/2} (Eq. value_min_max); c = index of f_i. */
+template <int c>
+__device__ __forceinline__ void mp_bounds(const double* v, const SchemeDev& S, double& fmin, double& fmax) {
+  const double dm1 = v[c] - 2.0 * v[c - 1] + v[c - 2];   /* d_{i-1} (Eq. curvature) */
+  const double d0 = v[c + 1] - 2.0 * v[c] + v[c - 1];    /* d_i */
+  const double dp1 = v[c + 2] - 2.0 * v[c + 1] + v[c];   /* d_{i+1} */
+  double dhp, dhm;
+  if (S.mp_curv == CURV_M4) {                            /* Eq. maximal_curvature */
+    dhp = minmod4(4.0 * d0 - dp1, 4.0 * dp1 - d0, d0, dp1);
+    dhm = minmod4(4.0 * dm1 - d0, 4.0 * d0 - dm1, dm1, d0);
+  } else {
+    dhp = minmod2(d0, dp1);
+    dhm = minmod2(dm1, d0);
+  }
+  const double fi = v[c], fip = v[c + 1], fim = v[c - 1];
+  const double f_ul = fi + S.mp_alpha * (fi - fim);          /* Eq. upper_limiter */
+  const double f_md = 0.5 * (fi + fip) - 0.5 * dhp;          /* Eq. median_value */
+  const double f_lc = fi + 0.5 * (fi - fim) + S.mp_beta_third * dhm;  /* Eq. large_curvature */
+  fmin = dmax(dmin(dmin(fi, fip), f_md), dmin(dmin(fi, f_ul), f_lc));
+  fmax = dmin(dmax(dmax(fi, fip), f_md), dmax(dmax(fi, f_ul), f_lc));
+}
+
+/* TVD5 flux f_i + phi delta^-/2 in difference form: with D_m = f_m - f_{m-1} and
+   B = (-2 D_{i-1} + 11 D_i + 24 D_{i+1} - 3 D_{i+2})/30, phi delta^- is
+   max(0, min(2D_i, 2D_{i+1}, B)) for D_i > 0, min(0, max(...)) for D_i < 0, 0 for D_i = 0. */
+template <int c>
+__device__ __forceinline__ double tvd5_flux(const double* v) {
+  const double Dm = v[c - 1] - v[c - 2], D0 = v[c] - v[c - 1], Dp = v[c + 1] - v[c], Dpp = v[c + 2] - v[c + 1];
+  const double B = (-2.0 * Dm + 11.0 * D0 + 24.0 * Dp - 3.0 * Dpp) / 30.0;
+  double pd = 0.0;
+  if (D0 > 0.0) pd = dmax(0.0, dmin(dmin(2.0 * D0, 2.0 * Dp), B));
+  else if (D0 < 0.0) pd = dmin(0.0, dmax(dmax(2.0 * D0, 2.0 * Dp), B));
+  return v[c] + 0.5 * pd;
+}
+
+/* Van Albada flux (Eqs. van_Albada_limiter, slop_ratio, vAflux, kappa = 1/3). */
+template <int c>
+__device__ __forceinline__ double va_flux(const double* v) {
+  const double dm = v[c] - v[c - 1], dp = v[c + 1] - v[c];
+  const double den = dp * dp + dm * dm;
+  const double phi = den > 0.0 ? 2.0 * dp * dm / den : 0.0;
+  const double kap = 1.0 / 3.0;
+  return v[c] + phi / 4.0 * ((1.0 - kap * phi) * dm + (1.0 + kap * phi) * dp);
+}
+
+/* Adaptive C_T of TENO8A (Section 2.4); returns C_T and [beta] in *e. */
+template <int c>
+__device__ __forceinline__ double adaptive_ct(const double* D, int* e) {
+  const double xi = 1e-3, Cr = 0.23, a1 = 10.5, a2 = 3.5;
+  const double eps = 0.9 * Cr / (1.0 - 0.9 * Cr) * xi * xi;
+  double eh = 0.0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    /* eta_{i-1+q}: Delta f_{j+1/2} = D[c + j], Delta f_{j-1/2} = D[c + j - 1] with j = q - 1 */
+    const double dfp = D[c + q - 1], dfm = D[c + q - 2];
+    const double eta = (fabs(2.0 * dfp * dfm) + eps) / (dfp * dfp + dfm * dfm + eps);
+    eh = (q == 0) ? eta : dmin(eh, eta);
+  }
+  const double m = 1.0 - dmin(1.0, eh / Cr);
+  const double om = 1.0 - m;
+  const double g = om * om * om * om * (1.0 + 4.0 * m);
+  const double beta = a1 - a2 * (1.0 - g);
+  int ex = (int)floor(beta);
+  ex = ex < 7 ? 7 : (ex > 10 ? 10 : ex);
+  *e = ex;
+  return ex == 7 ? 1e-7 : (ex == 8 ? 1e-8 : (ex == 9 ? 1e-9 : 1e-10));
+}
+
+/* One TENO-M reconstruction.  flag receives delta bits | ([beta]-7) << 6; st receives
+   ST_NONFINITE when an indicator is not finite. */
+template <int K, int LIM>
+__device__ __forceinline__ double teno_m(const double (&v)[K], const SchemeDev& S, unsigned& flag, int& st) {
+  constexpr int c = K / 2 - 1;  /* index of f_i */
+  constexpr int nk = K - 2;
+  double D[K - 1];
+#pragma unroll
+  for (int t = 0; t < K - 1; ++t) D[t] = v[t + 1] - v[t];
+  double fk[nk], bk[nk];
+  fk[0] = cand0<c>(v);
+  fk[1] = cand1<c>(v);
+  fk[2] = cand2<c>(v);
+  fk[3] = cand3<c>(v);
+  bk[0] = beta0<c - 1>(D);
+  bk[1] = beta1<c>(D);
+  bk[2] = beta2<c - 2>(D);
+  bk[3] = beta3<c>(D);
+  double bK;
+  if constexpr (K == 8) {
+    fk[4] = cand4<c>(v);
+    fk[5] = cand5<c>(v);
+    bk[4] = beta4<c - 3>(D);
+    bk[5] = beta5<c>(D);
+    bK = betaK8<0>(D);
+  } else {
+    bK = betaK6<0>(D);
+  }
+  const double tau = fabs(bK - (bk[1] + bk[2] + 4.0 * bk[0]) / 6.0);
+  double gk[nk], sum = 0.0;
+#pragma unroll
+  for (int k = 0; k < nk; ++k) {
+    const double x = 1.0 + tau / (bk[k] + 1e-40);
+    const double x3 = x * x * x;
+    gk[k] = x3 * x3;
+    sum += gk[k];
+  }
+  double CT = S.ct_const;
+  int ex = 7;
+  if (S.ct_mode == CT_ADAPTIVE) CT = adaptive_ct<c>(D, &ex);
+  unsigned bits = 0;
+#pragma unroll
+  for (int k = 0; k < nk; ++k) bits |= (gk[k] / sum < CT ? 0u : 1u) << k;
+  if (!isfinite(sum)) st |= ST_NONFINITE;
+  flag = bits | ((unsigned)((ex - 7) & 3) << 6);
+  if (S.weights == W_TENO) {
+    double num = 0.0, den = 0.0;
+#pragma unroll
+    for (int k = 0; k < nk; ++k)
+      if (bits >> k & 1u) { num += S.d[k] * fk[k]; den += S.d[k]; }
+    return num / den;
+  }
+  if (bits != (1u << nk) - 1u) {
+    if constexpr (LIM == LIM_MP) {
+      double fmin, fmax;
+      mp_bounds<c>(v, S, fmin, fmax);
+#pragma unroll
+      for (int k = 0; k < nk; ++k)
+        if (!(bits >> k & 1u)) fk[k] = median3(fk[k], fmin, fmax);
+    } else {
+      const double fl = (LIM == LIM_TVD5) ? tvd5_flux<c>(v) : va_flux<c>(v);
+#pragma unroll
+      for (int k = 0; k < nk; ++k)
+        if (!(bits >> k & 1u)) fk[k] = fl;
+    }
+  }
+  double f = 0.0;
+#pragma unroll
+  for (int k = 0; k < nk; ++k) f += S.d[k] * fk[k];
+  return f;
+}
+
+}  // namespace tenom

@@ -1,0 +1,242 @@
+"""Python binding of the C ABI in include/tenom.h (argument marshalling only).
+
+Every step of the method runs in libtenom.so's CUDA kernels; this module only converts
+torch tensors to device pointers and streams.  If the library is missing it raises:
+there is no CPU fallback.  PyTorch provides device memory and streams.
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtenom.so")
+
+TENOM_OK, TENOM_E_INVALID, TENOM_E_CUDA, TENOM_E_NONPHYSICAL, TENOM_E_TIMEOUT, TENOM_E_UNSUPPORTED = range(6)
+BC_PERIODIC, BC_TRANSMISSIVE = 0, 1
+LIM_MP, LIM_TVD5, LIM_VA = 0, 1, 2
+CT_CONST, CT_ADAPTIVE = 0, 1
+CURV_M4, CURV_MM = 0, 1
+W_TENOM, W_TENO = 0, 1
+ST_RHO, ST_P, ST_ROE, ST_NONFINITE = 1, 2, 4, 8
+
+
+class tenom_grid(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("dx", ctypes.c_double * 3),
+                ("bc", ctypes.c_int * 3), ("gamma", ctypes.c_double)]
+
+
+class tenom_scheme(ctypes.Structure):
+    _fields_ = [("K", ctypes.c_int), ("limiter", ctypes.c_int), ("ct_mode", ctypes.c_int),
+                ("ct_const", ctypes.c_double), ("mp_alpha", ctypes.c_double), ("mp_beta", ctypes.c_double),
+                ("mp_curv", ctypes.c_int), ("weights", ctypes.c_int), ("d", ctypes.c_double * 6)]
+
+
+class TenomError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("tenom status %d: %s" % (status, msg))
+        self.status = status
+
+
+_lib = None
+VP = ctypes.c_void_p
+
+
+def lib():
+    """Load libtenom.so (build it first with __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libtenom.so not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        c_int, c_double, P = ctypes.c_int, ctypes.c_double, ctypes.POINTER
+        L.tenom_scheme_default.argtypes = [P(tenom_scheme), c_int]
+        L.tenom_create.argtypes = [P(VP), P(tenom_grid), P(tenom_scheme), VP]
+        L.tenom_destroy.argtypes = [VP]
+        L.tenom_init_state.argtypes = [VP, VP, VP]
+        L.tenom_rhs.argtypes = [VP, VP, VP]
+        L.tenom_max_dt.argtypes = [VP, VP, c_double, VP]
+        L.tenom_rk3_step.argtypes = [VP, VP, VP]
+        L.tenom_advance.argtypes = [VP, VP, VP, c_double, c_double, c_int]
+        L.tenom_advance_host.argtypes = [VP, VP, VP, P(c_double), c_double, c_double, c_int]
+        L.tenom_face_dump.argtypes = [VP, VP, c_int, VP, VP]
+        L.tenom_status_word.argtypes = [VP, P(c_int), c_int]
+        L.tenom_last_error.argtypes = [VP]
+        L.tenom_last_error.restype = ctypes.c_char_p
+        L.tenom_kernel_timing.argtypes = [VP, c_int, P(c_double), P(ctypes.c_longlong)]
+        L.tenom_fp64_peak.argtypes = [VP, c_int, c_int, P(c_double)]
+        for name in ("tenom_scheme_default", "tenom_create", "tenom_destroy", "tenom_init_state", "tenom_rhs",
+                     "tenom_max_dt", "tenom_rk3_step", "tenom_advance", "tenom_advance_host", "tenom_face_dump",
+                     "tenom_status_word", "tenom_kernel_timing", "tenom_fp64_peak"):
+            getattr(L, name).restype = c_int
+        _lib = L
+    return _lib
+
+
+def make_grid(shape, dx, bc, gamma=1.4):
+    """shape, dx, bc listed x-first."""
+    g = tenom_grid()
+    g.dim = len(shape)
+    for a in range(3):
+        g.n[a] = int(shape[a]) if a < len(shape) else 1
+        g.dx[a] = float(dx[a]) if a < len(shape) else 1.0
+        g.bc[a] = int(bc[a]) if a < len(shape) else BC_PERIODIC
+    g.gamma = gamma
+    return g
+
+
+def make_scheme(K=6, limiter=LIM_MP, ct_mode=None, ct_const=1e-5, mp_alpha=1.25, mp_beta=4.0, mp_curv=CURV_M4,
+                weights=W_TENOM, d=None):
+    s = tenom_scheme()
+    st = lib().tenom_scheme_default(ctypes.byref(s), K)
+    if st != TENOM_OK:
+        raise TenomError(st, "tenom_scheme_default(K=%d)" % K)
+    s.limiter = limiter
+    if ct_mode is not None:
+        s.ct_mode = ct_mode
+    s.ct_const = ct_const
+    s.mp_alpha = mp_alpha
+    s.mp_beta = mp_beta
+    s.mp_curv = mp_curv
+    s.weights = weights
+    if d is not None:
+        for k in range(6):
+            s.d[k] = d[k] if k < len(d) else 0.0
+    return s
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Solver:
+    """One grid + scheme bound to the current torch CUDA stream.
+
+    State tensors are torch float64 CUDA tensors of shape (nvar, nz, ny, nx) with the
+    leading singleton spatial axes dropped (1D: (3, nx); 2D: (4, ny, nx))."""
+
+    def __init__(self, shape, dx, bc, scheme=None, gamma=1.4, stream=None):
+        import torch
+        self.shape = tuple(int(n) for n in shape)
+        self.dim = len(self.shape)
+        self.nv = self.dim + 2
+        self.grid = make_grid(self.shape, dx, bc, gamma)
+        self.scheme = scheme if scheme is not None else make_scheme(6)
+        self._ctx = ctypes.c_void_p()
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        st = lib().tenom_create(ctypes.byref(self._ctx), ctypes.byref(self.grid), ctypes.byref(self.scheme),
+                                ctypes.c_void_p(self.stream.cuda_stream))
+        if st != TENOM_OK:
+            raise TenomError(st, "tenom_create")
+        self.dt = torch.zeros(1, dtype=torch.float64, device="cuda")
+        self.t = torch.zeros(1, dtype=torch.float64, device="cuda")
+
+    # numpy-style (z, y, x) shape of the state
+    @property
+    def state_shape(self):
+        return (self.nv,) + tuple(reversed(self.shape))
+
+    def face_shape(self, axis):
+        n = list(self.shape)
+        n[axis] += 1
+        return tuple(reversed(n))
+
+    def _check(self, st, what):
+        if st != TENOM_OK:
+            msg = lib().tenom_last_error(self._ctx)
+            raise TenomError(st, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    def close(self):
+        if self._ctx:
+            lib().tenom_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def tensor(self):
+        import torch
+        return torch.empty(self.state_shape, dtype=torch.float64, device="cuda")
+
+    def init_state(self, prim):
+        """prim: float64 CUDA tensor (rho, u.., p) -> conserved state tensor."""
+        U = self.tensor()
+        self._check(lib().tenom_init_state(self._ctx, _ptr(prim), _ptr(U)), "tenom_init_state")
+        return U
+
+    def rhs(self, U, out=None):
+        out = self.tensor() if out is None else out
+        self._check(lib().tenom_rhs(self._ctx, _ptr(U), _ptr(out)), "tenom_rhs")
+        return out
+
+    def max_dt(self, U, cfl=0.4, out=None):
+        out = self.dt if out is None else out
+        self._check(lib().tenom_max_dt(self._ctx, _ptr(U), cfl, _ptr(out)), "tenom_max_dt")
+        return out
+
+    def rk3_step(self, U, dt_dev):
+        self._check(lib().tenom_rk3_step(self._ctx, _ptr(U), _ptr(dt_dev)), "tenom_rk3_step")
+        return U
+
+    def advance(self, U, nsteps, t_end=math.inf, cfl=0.4, t_dev=None):
+        t_dev = self.t if t_dev is None else t_dev
+        self._check(lib().tenom_advance(self._ctx, _ptr(U), _ptr(t_dev), t_end, cfl, nsteps), "tenom_advance")
+        return U
+
+    def advance_host(self, U_host_in, U_host_out, t=0.0, t_end=math.inf, cfl=0.4, nsteps=1):
+        """Host buffers (numpy float64, C-contiguous, or pinned torch CPU tensors)."""
+        tt = ctypes.c_double(t)
+
+        def hp(a):
+            if isinstance(a, np.ndarray):
+                assert a.dtype == np.float64 and a.flags.c_contiguous
+                return ctypes.c_void_p(a.ctypes.data)
+            return ctypes.c_void_p(a.data_ptr())
+        self._check(lib().tenom_advance_host(self._ctx, hp(U_host_in), hp(U_host_out), ctypes.byref(tt), t_end, cfl,
+                                             nsteps), "tenom_advance_host")
+        return tt.value
+
+    def face_dump(self, U, axis, flags=True):
+        import torch
+        F = torch.empty((self.nv,) + self.face_shape(axis), dtype=torch.float64, device="cuda")
+        fl = torch.zeros(self.face_shape(axis) + (self.nv, 2), dtype=torch.uint8, device="cuda") if flags else None
+        self._check(lib().tenom_face_dump(self._ctx, _ptr(U), axis, _ptr(F), _ptr(fl) if fl is not None else None),
+                    "tenom_face_dump")
+        return F, fl
+
+    def status(self, reset=False):
+        v = ctypes.c_int(0)
+        st = lib().tenom_status_word(self._ctx, ctypes.byref(v), 1 if reset else 0)
+        if st not in (TENOM_OK, TENOM_E_NONPHYSICAL):
+            self._check(st, "tenom_status_word")
+        return v.value
+
+    def kernel_timing(self, enable):
+        ms = ctypes.c_double(0)
+        n = ctypes.c_longlong(0)
+        self._check(lib().tenom_kernel_timing(self._ctx, 1 if enable else 0, ctypes.byref(ms), ctypes.byref(n)),
+                    "tenom_kernel_timing")
+        return ms.value, n.value
+
+
+def fp64_peak(nblocks=152 * 8, iters=4096):
+    f = ctypes.c_double(0)
+    st = lib().tenom_fp64_peak(_stream(), nblocks, iters, ctypes.byref(f))
+    if st != TENOM_OK:
+        raise TenomError(st, "tenom_fp64_peak")
+    return f.value
