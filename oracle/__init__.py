@@ -96,9 +96,9 @@ def lib():
         L.orc_recon.argtypes = [sp, dp, c_int, dp, ip, ip, dp, dp]
         L.orc_recon_parts.argtypes = [sp, dp, dp, dp, dp, dp, dp, dp, dp, dp]
         L.orc_init_state.argtypes = [gp, dp, dp]
-        L.orc_faces.argtypes = [gp, sp, dp, c_int, dp, u8p, dp, dp]
+        L.orc_faces.argtypes = [gp, sp, dp, c_int, dp, u8p, dp, dp, dp]
         L.orc_faces.restype = c_int
-        L.orc_faces_at.argtypes = [gp, sp, dp, c_int, ip, c_int, dp, u8p, dp, dp]
+        L.orc_faces_at.argtypes = [gp, sp, dp, c_int, ip, c_int, dp, u8p, dp, dp, dp]
         L.orc_faces_at.restype = c_int
         L.orc_rhs.argtypes = [gp, sp, dp, dp]
         L.orc_rhs.restype = c_int
@@ -183,11 +183,12 @@ def face_shape(grid, axis):
     return tuple(reversed(n))
 
 
-def faces(grid, scheme, U, axis):
+def faces(grid, scheme, U, axis, with_scale=False):
     """All face fluxes of one axis: (Fhat[nv, *face_shape], flags[*face_shape, nv, 2],
     cut[*face_shape, nv, 2], noise[*face_shape, nv, 2], bad).  flags = delta bits | ct code << 6;
     cut = distance of the cutoff decision from its threshold (relative); noise = rounding-noise
-    ratio of the reconstructed sequence."""
+    ratio of the reconstructed sequence; scale[nv, *face_shape] (with_scale=True) = magnitude of
+    the terms of the back-projection sum sum_s r_s (f+_s + f-_s)."""
     U = _c(U)
     fs = face_shape(grid, axis)
     nv = nvar(grid)
@@ -195,12 +196,15 @@ def faces(grid, scheme, U, axis):
     fl = np.zeros(fs + (nv, 2), dtype=np.uint8)
     cut = np.zeros(fs + (nv, 2))
     noise = np.zeros(fs + (nv, 2))
+    scale = np.zeros((nv,) + fs)
     bad = lib().orc_faces(ctypes.byref(grid), ctypes.byref(scheme), _d(U), axis, _d(F),
-                          fl.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _d(cut), _d(noise))
+                          fl.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _d(cut), _d(noise), _d(scale))
+    if with_scale:
+        return F, fl, cut, noise, bad, scale
     return F, fl, cut, noise, bad
 
 
-def faces_at(grid, scheme, U, axis, idx):
+def faces_at(grid, scheme, U, axis, idx, with_scale=False):
     """Face fluxes at selected faces; idx[n, 3] = (x, y, z) with the face index on `axis`."""
     U = _c(U)
     idx = _c(idx, np.int32)
@@ -210,9 +214,12 @@ def faces_at(grid, scheme, U, axis, idx):
     fl = np.zeros((n, nv, 2), dtype=np.uint8)
     cut = np.zeros((n, nv, 2))
     noise = np.zeros((n, nv, 2))
+    scale = np.zeros((n, nv))
     bad = lib().orc_faces_at(ctypes.byref(grid), ctypes.byref(scheme), _d(U), axis,
                              idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), n, _d(F),
-                             fl.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _d(cut), _d(noise))
+                             fl.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _d(cut), _d(noise), _d(scale))
+    if with_scale:
+        return F, fl, cut, noise, bad, scale
     return F, fl, cut, noise, bad
 
 

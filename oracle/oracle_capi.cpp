@@ -70,16 +70,17 @@ void orc_init_state(const Grid* g, const double* prim, double* U) {
 }
 
 int orc_faces(const Grid* g, const Scheme* s, const double* U, int axis, double* Fhat, uint8_t* flags,
-              double* cut, double* noise) {
+              double* cut, double* noise, double* scale) {
   Grid G = norm_grid(g);
   Scheme S = norm_scheme(s);
-  return all_faces<double>(G, S, U, axis, Fhat, flags, cut, noise);
+  return all_faces<double>(G, S, U, axis, Fhat, flags, cut, noise, scale);
 }
 
 /* Face fluxes at a list of faces only (sampled parity at full size).
    faces: [n][3] cell multi-index with the face index on the axis component. */
 int orc_faces_at(const Grid* g, const Scheme* s, const double* U, int axis, const int* faces, int n,
-                 double* Fhat /* [n][nv] */, uint8_t* flags /* [n][nv][2] */, double* cut, double* noise) {
+                 double* Fhat /* [n][nv] */, uint8_t* flags /* [n][nv][2] */, double* cut, double* noise,
+                 double* scale /* [n][nv] */) {
   Grid G = norm_grid(g);
   Scheme S = norm_scheme(s);
   const int nv = G.dim + 2;
@@ -89,7 +90,10 @@ int orc_faces_at(const Grid* g, const Scheme* s, const double* U, int axis, cons
     FaceDiag dg;
     double F[5];
     face_flux<double>(G, S, U, axis, idx, idx[axis], F, &dg);
-    for (int v = 0; v < nv; ++v) Fhat[q * nv + v] = F[v];
+    for (int v = 0; v < nv; ++v) {
+      Fhat[q * nv + v] = F[v];
+      if (scale) scale[q * nv + v] = dg.scale[v];
+    }
     for (int v = 0; v < nv; ++v)
       for (int sd = 0; sd < 2; ++sd) {
         int o = (q * nv + v) * 2 + sd;

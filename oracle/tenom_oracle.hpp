@@ -470,19 +470,33 @@ struct FaceDiag {
   double noise[5][2];     /* rounding-noise ratio of the sequence: 2^-52 max|g_m| over
                              max|g_m - g_i| (0 for an exactly constant sequence); where it
                              is large the cutoff decision is set by rounding, not data */
+  double scale[5];        /* per component, sum over fields s of |R_{v,s}| (|f+_s| + |f-_s|):
+                             the magnitude of the terms of the back-projection sum */
   int nonphysical;
 };
 
-/* Rounding-noise ratio of a K-point sequence (diagnostic only). */
+/* Rounding-noise ratio of a K-point sequence (diagnostic only): the largest, over the
+   candidate stencils and the full stencil, of 2^-52 max|g| / (spread of the stencil's
+   values about g_i); infinite when a stencil's values are all equal.  Where it is large,
+   some beta_k is made of rounding noise and the cutoff decision is set by rounding. */
 template <class T>
-inline double noise_ratio(const T* g, int K, int ii) {
-  double mx = 0.0, dv = 0.0;
-  for (int q = 0; q < K; ++q) {
-    mx = std::fmax(mx, std::fabs(val(g[q])));
-    dv = std::fmax(dv, std::fabs(val(g[q]) - val(g[ii])));
+inline double noise_ratio(const T* g, int K) {
+  const int h = K / 2;
+  double mx = 0.0;
+  for (int q = 0; q < K; ++q) mx = std::fmax(mx, std::fabs(val(g[q])));
+  const int j0s[7] = {ORC_S0_J0, ORC_S1_J0, ORC_S2_J0, ORC_S3_J0, ORC_S4_J0, ORC_S5_J0,
+                      K == 6 ? ORC_F6_J0 : ORC_F8_J0};
+  const int rs[7] = {ORC_S0_R, ORC_S1_R, ORC_S2_R, ORC_S3_R, ORC_S4_R, ORC_S5_R, K == 6 ? ORC_F6_R : ORC_F8_R};
+  const double gi = val(g[h - 1]);
+  double worst = 0.0;
+  for (int k = 0; k < 7; ++k) {
+    if (k < 6 && k >= K - 2) continue;
+    double dv = 0.0;
+    for (int m = 0; m < rs[k]; ++m) dv = std::fmax(dv, std::fabs(val(g[j0s[k] + m + h - 1]) - gi));
+    double r = (dv == 0.0) ? (mx == 0.0 ? 0.0 : HUGE_VAL) : 2.220446049250313e-16 * mx / dv;
+    worst = std::fmax(worst, r);
   }
-  if (dv == 0.0) return 0.0;
-  return 2.220446049250313e-16 * mx / dv;
+  return worst;
 }
 
 /* Numerical flux at face f (between cells f-1 and f) along axis a of the pencil whose
@@ -516,6 +530,7 @@ inline void face_flux(const Grid& g, const Scheme& S, const T* U, int a, const i
   for (int q = 0; q < K; ++q)
     if (diag && (val(P[q].p) <= 0 || val(P[q].rho) <= 0)) diag->nonphysical = 1;
   T fsum[5];
+  double fabs_sum[5] = {0, 0, 0, 0, 0};
   for (int s = 0; s < nv; ++s) {
     /* characteristic variables and fluxes of field s at the K points */
     T W[8], G[8], lam[8];
@@ -544,8 +559,11 @@ inline void face_flux(const Grid& g, const Scheme& S, const T* U, int a, const i
     T fminus = teno_m<T>(S, [&](int m) { return gm[h - m]; }, &dm);
     fsum[s] = fplus + fminus;
     if (diag) {
+      fabs_sum[s] = std::fabs(val(fplus)) + std::fabs(val(fminus));
       ReconDiag* dd[2] = {&dp, &dm};
-      const T* seq[2] = {gp, gm};
+      T gmr[8];  /* the f- sequence in the mirrored order it is reconstructed in */
+      for (int q = 0; q < K; ++q) gmr[q] = gm[K - 1 - q];
+      const T* seq[2] = {gp, gmr};
       for (int side = 0; side < 2; ++side) {
         int code = (S.ct_mode == CT_ADAPTIVE) ? (dd[side]->ct_exp - 7) & 3 : 0;
         diag->flags[s][side] = (uint8_t)(dd[side]->delta_bits | (code << 6));
@@ -556,7 +574,7 @@ inline void face_flux(const Grid& g, const Scheme& S, const T* U, int a, const i
           c = std::fmin(c, std::fabs(b - std::floor(b + 0.5)) / b);
         }
         diag->cut[s][side] = c;
-        diag->noise[s][side] = noise_ratio(seq[side], K, h - 1);
+        diag->noise[s][side] = noise_ratio(seq[side], K);
         if (dd[side]->nonfinite) diag->nonphysical = 1;
       }
     }
@@ -564,8 +582,13 @@ inline void face_flux(const Grid& g, const Scheme& S, const T* U, int a, const i
   /* back-projection F = sum_s r_s (f+_s + f-_s) */
   for (int v = 0; v < nv; ++v) {
     T acc = 0.0;
-    for (int s = 0; s < nv; ++s) acc = acc + E.R[v][s] * fsum[s];
+    double sc = 0.0;
+    for (int s = 0; s < nv; ++s) {
+      acc = acc + E.R[v][s] * fsum[s];
+      sc += std::fabs(val(E.R[v][s])) * fabs_sum[s];
+    }
     Fhat[v] = acc;
+    if (diag) diag->scale[v] = sc;
   }
 }
 
@@ -581,7 +604,7 @@ inline long long nface(const Grid& g, int a) {
    be null; see FaceDiag). */
 template <class T>
 inline int all_faces(const Grid& g, const Scheme& S, const T* U, int a, T* Fhat, uint8_t* flags,
-                     double* cut, double* noise) {
+                     double* cut, double* noise, double* scale = nullptr) {
   const int D = g.dim, nv = D + 2;
   int fn[3] = {1, 1, 1};
   for (int d = 0; d < D; ++d) fn[d] = (d == a) ? g.n[d] + 1 : g.n[d];
@@ -595,7 +618,10 @@ inline int all_faces(const Grid& g, const Scheme& S, const T* U, int a, T* Fhat,
         T F[5];
         FaceDiag dg;
         face_flux<T>(g, S, U, a, idx, idx[a], F, &dg);
-        for (int v = 0; v < nv; ++v) Fhat[v * nf + lin] = F[v];
+        for (int v = 0; v < nv; ++v) {
+          Fhat[v * nf + lin] = F[v];
+          if (scale) scale[v * nf + lin] = dg.scale[v];
+        }
         for (int v = 0; v < nv; ++v)
           for (int s = 0; s < 2; ++s) {
             long long o = (lin * nv + v) * 2 + s;

@@ -213,6 +213,9 @@ class Solver:
 
     def face_dump(self, U, axis, flags=True):
         import torch
+        if not 0 <= axis < self.dim:  # let the library reject it
+            dummy = torch.empty(1, dtype=torch.float64, device="cuda")
+            self._check(lib().tenom_face_dump(self._ctx, _ptr(U), axis, _ptr(dummy), None), "tenom_face_dump")
         F = torch.empty((self.nv,) + self.face_shape(axis), dtype=torch.float64, device="cuda")
         fl = torch.zeros(self.face_shape(axis) + (self.nv, 2), dtype=torch.uint8, device="cuda") if flags else None
         self._check(lib().tenom_face_dump(self._ctx, _ptr(U), axis, _ptr(F), _ptr(fl) if fl is not None else None),

@@ -64,11 +64,13 @@ def test_face_flux_parity(T, orc, shape, bc, K, lim, jumps):
     sw = []
     for a in range(len(shape)):
         Fg, flg = S.face_dump(Ug, a)
-        Fo, flo, cut, noise, bad = orc.faces(g, so, Uo, a)
+        Fo, flo, cut, noise, bad, scale = orc.faces(g, so, Uo, a, with_scale=True)
         assert bad == 0
-        st = compare_faces(Fg.cpu().numpy(), flg.cpu().numpy(), Fo, flo, cut, noise,
+        st = compare_faces(Fg.cpu().numpy(), flg.cpu().numpy(), Fo, flo, cut, noise, scale,
                            label="%s axis %d" % (shape, a))
-        assert st["switch_faces"] <= max(2, 0.02 * st["faces"]), st
+        # near-cutoff switches are rare; noise-decided ones sit where a characteristic field
+        # is flat to rounding (transmissive ghost copies, degenerate fields)
+        assert st["near_cutoff_faces"] <= max(2, 0.01 * st["faces"]), st
         Fs.append(Fo)
         sw.append((flg.cpu().numpy() != flo).reshape(flo.shape[:-2] + (-1,)).any(axis=-1))
     ro, _ = orc.rhs(g, so, Uo)
@@ -149,8 +151,8 @@ def test_degenerate_sizes(T, orc, shape, bc, K):
     S, g, so, Uo, Ug = setup(T, orc, shape, bc, K, 0, prim)
     for a in range(len(shape)):
         Fg, flg = S.face_dump(Ug, a)
-        Fo, flo, cut, noise, bad = orc.faces(g, so, Uo, a)
-        compare_faces(Fg.cpu().numpy(), flg.cpu().numpy(), Fo, flo, cut, noise, label="%s" % (shape,))
+        Fo, flo, cut, noise, bad, scale = orc.faces(g, so, Uo, a, with_scale=True)
+        compare_faces(Fg.cpu().numpy(), flg.cpu().numpy(), Fo, flo, cut, noise, scale, label="%s" % (shape,))
 
 
 def test_invalid_arguments_rejected(T):
@@ -198,10 +200,10 @@ def check_sampled(T, orc, S, g, so, Ug, Uo, shape, m, seed):
         Fg = Fg.cpu().numpy()
         flg = flg.cpu().numpy()
         idx = sample_faces(rng, shape, a, m)
-        Fo, flo, cut, noise, bad = orc.faces_at(g, so, Uo, a, idx)
+        Fo, flo, cut, noise, bad, scale = orc.faces_at(g, so, Uo, a, idx, with_scale=True)
         sel = tuple(idx[:, d] for d in reversed(range(len(shape))))
         Fgs = np.stack([Fg[v][sel] for v in range(len(shape) + 2)])
-        compare_faces(Fgs, flg[sel], Fo.T, flo, cut, noise, label="sampled axis %d" % a)
+        compare_faces(Fgs, flg[sel], Fo.T, flo, cut, noise, scale.T, label="sampled axis %d" % a)
         # the face fluxes of all faces must be finite
         assert np.isfinite(Fg).all()
         del Fg, flg
