@@ -127,6 +127,32 @@ tenom_status tenom_advance_host(tenom_ctx* ctx, const double* U_host_in, double*
  * [beta] - 7 of Eq. cut-off_adjust when C_T is adaptive.  flags may be NULL. */
 tenom_status tenom_face_dump(tenom_ctx* ctx, const double* U, int axis, double* Fhat, uint8_t* flags);
 
+/* Size of the static device scratch of tenom_rhs_noalloc: 16 MiB, held on every GPU that
+ * loads this library until the process exits. */
+#define TENOM_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* tenom_rhs without a context and without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that must not allocate device memory
+ * once they are running -- code living inside another framework's memory pool or
+ * allocator hook, or a latency-critical loop that cannot accept the implicit device
+ * synchronisation of cudaMalloc/cudaFree.  It computes dUdt = L(U) exactly like tenom_rhs
+ * (same kernels) for the given grid and scheme, on `stream` (a cudaStream_t; NULL = legacy
+ * default stream).  U and dUdt are caller-owned device arrays as for tenom_rhs; status_dev
+ * is an optional caller-owned device int that receives TENOM_ST_* bits (ORed in, the
+ * caller clears it); with NULL the bits go to a word inside the scratch and are not
+ * reported.
+ * Scratch: the face fluxes of every axis live in one file-scope static device array of
+ * TENOM_NOALLOC_SCRATCH_BYTES; a grid needing more -- (dim+2) * sum_a nface_a * 8 bytes
+ * plus 256 -- is rejected with TENOM_E_INVALID and a message on stderr (for 2D that is
+ * about 260,000 cells).  The array's device address is looked up the first time the
+ * entry point runs on a device (cudaGetSymbolAddress, with that device current); make
+ * that first call before any stream capture.  Every call, on every stream and host
+ * thread, shares the one array and it keeps the last call's contents, so calls whose
+ * kernels overlap on the GPU race: order them on one stream or synchronise between them.
+ * Returns TENOM_E_CUDA if a launch fails. */
+tenom_status tenom_rhs_noalloc(const tenom_grid* grid, const tenom_scheme* scheme, const double* U, double* dUdt,
+                               int* status_dev, void* stream);
+
 /* Sticky device status word (TENOM_ST_* bits); synchronises the stream.  reset != 0 clears it. */
 tenom_status tenom_status_word(tenom_ctx* ctx, int* status_host, int reset);
 

@@ -588,3 +588,41 @@ tenom_status tenom_fp64_peak(void* stream, int nblocks, int iters, double* flops
 }
 
 }  // extern "C"
+
+/* ---------------------------------------------------------------- helpers for other units */
+namespace tenom {
+
+tenom_status check_grid_scheme(const tenom_grid* g, const tenom_scheme* s, std::string* msg) {
+  return validate(g, s, msg);
+}
+
+SchemeDev scheme_for_device(const tenom_scheme& s) {
+  tenom_scheme t = s;
+  bool anyd = false;
+  for (int k = 0; k < 6; ++k) anyd |= (t.d[k] != 0.0);
+  if (!anyd)
+    for (int k = 0; k < t.K - 2; ++k) t.d[k] = (t.K == 6) ? kDopt6[k] : kDopt8[k];
+  return scheme_dev(t);
+}
+
+cudaError_t launch_rhs_divergence(int nv, double* const F[3], const int n[3], const double dx[3], long long ncell,
+                                  const long long nface[3], double* out, cudaStream_t st) {
+  StageArgs a;
+  memset(&a, 0, sizeof(a));
+  for (int d = 0; d < 3; ++d) {
+    a.F[d] = F[d];
+    a.n[d] = n[d];
+    a.dx[d] = dx[d];
+    a.nface[d] = nface[d];
+  }
+  a.out = out;
+  a.ncell = ncell;
+  a.mode = 0;
+  unsigned nb = ew_blocks(ncell);
+  if (nv == 3) stage_kernel<3><<<nb, 256, 0, st>>>(a);
+  else if (nv == 4) stage_kernel<4><<<nb, 256, 0, st>>>(a);
+  else stage_kernel<5><<<nb, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace tenom

@@ -26,3 +26,16 @@ inline void face_grid(int nv, int axis, const int* n, int K, dim3* grid, dim3* b
 }
 
 }  // namespace tenom
+
+#include <string>
+#include "tenom.h"
+
+namespace tenom {
+/* Argument checks of tenom_create, usable without a context. */
+tenom_status check_grid_scheme(const tenom_grid* g, const tenom_scheme* s, std::string* msg);
+/* Device copy of a scheme (all-zero d_k replaced by the maximal-order weights). */
+SchemeDev scheme_for_device(const tenom_scheme& s);
+/* dUdt = -sum_a (F_a[f+1] - F_a[f]) / dx_a from face buffers F[a] ([nv][nface_a]). */
+cudaError_t launch_rhs_divergence(int nv, double* const F[3], const int n[3], const double dx[3], long long ncell,
+                                  const long long nface[3], double* out, cudaStream_t st);
+}  // namespace tenom

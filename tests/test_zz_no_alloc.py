@@ -1,0 +1,65 @@
+"""tenom_rhs_noalloc: the operator L(U) for callers that must not allocate device memory
+while running (inside another framework's memory pool or allocator hook, or in a loop
+that cannot take cudaMalloc's implicit device synchronisation).  It keeps its face-flux
+scratch in a static device array instead of a context.  Checked through the C ABI against
+tenom_rhs on two calls in a row (the second call must not see the first one's scratch),
+and for its size limit.  This file is collected last on purpose."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2010_13289_gb300 import problems as PB
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2010_13289_gb300 import tenom
+    tenom.lib()
+    return tenom
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+@pytest.mark.parametrize("shape,bc,K,lim", [((96, 80), (0, 1), 6, 0), ((40, 24, 16), (0, 0, 1), 8, 1),
+                                            ((300,), (1,), 8, 0)])
+def test_noalloc_rhs_matches_tenom_rhs_twice(T, shape, bc, K, lim):
+    dx = tuple(1.0 / n for n in shape)
+    scheme = T.make_scheme(K, limiter=lim)
+    grid = T.make_grid(shape, dx, bc)
+    S = T.Solver(shape, dx, bc, scheme)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for seed in (1, 2):  # two calls in a row with different states
+        prim = PB.random_state(tuple(reversed(shape)), seed, jumps=True)
+        U = S.init_state(torch.from_numpy(prim).cuda())
+        want = S.rhs(U)
+        got = torch.full_like(want, float("nan"))
+        st = T.lib().tenom_rhs_noalloc(ctypes.byref(grid), ctypes.byref(scheme), _p(U), _p(got), _p(status),
+                                       stream)
+        assert st == T.TENOM_OK
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(got.cpu().numpy(), want.cpu().numpy(), rtol=1e-13, atol=1e-13)
+        assert status.item() == 0
+    S.close()
+
+
+def test_noalloc_rejects_grid_beyond_scratch(T):
+    shape = (1024, 1024)  # 4 * 2 * 1025 * 1024 doubles of faces: beyond the 16 MiB scratch
+    grid = T.make_grid(shape, (1e-3, 1e-3), (0, 0))
+    scheme = T.make_scheme(6)
+    U = torch.ones((4, 1024, 1024), dtype=torch.float64, device="cuda")
+    out = torch.zeros_like(U)
+    st = T.lib().tenom_rhs_noalloc(ctypes.byref(grid), ctypes.byref(scheme), _p(U), _p(out), None, None)
+    assert st == T.TENOM_E_INVALID
+    assert float(out.abs().max()) == 0.0  # nothing was launched
