@@ -160,6 +160,18 @@ __global__ void finalize_dt_kernel(unsigned long long* smax, double cfl, double*
 
 __global__ void advance_time_kernel(double* t, const double* dt) { *t = *t + *dt; }
 
+/* Compare the Newton-Raphson reciprocal / rsqrt with CUDA's correctly rounded 1.0/x, sqrt. */
+__global__ void fastmath_check_kernel(const double* x, double* out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    out[4 * i + 0] = rcp_nr(v);
+    out[4 * i + 1] = 1.0 / v;
+    const double r = rsqrt_nr(v);
+    out[4 * i + 2] = v * r;
+    out[4 * i + 3] = sqrt(v);
+  }
+}
+
 /* FP64 pipe probe: 8 independent FMA chains per thread. */
 __global__ void dfma_probe_kernel(int iters, double a, double b, double* sink) {
   double x[8];
@@ -561,6 +573,12 @@ tenom_status tenom_kernel_timing(tenom_ctx* c, int enable, double* face_ms_per_l
   c->ev_used = 0;
   c->timing = enable != 0;
   return TENOM_OK;
+}
+
+tenom_status tenom_check_fastmath(const double* x, double* out, long long n, void* stream) {
+  if (!x || !out || n < 0) return TENOM_E_INVALID;
+  fastmath_check_kernel<<<ew_blocks(n), 256, 0, (cudaStream_t)stream>>>(x, out, n);
+  return cudaGetLastError() == cudaSuccess ? TENOM_OK : TENOM_E_CUDA;
 }
 
 tenom_status tenom_fp64_peak(void* stream, int nblocks, int iters, double* flops) {

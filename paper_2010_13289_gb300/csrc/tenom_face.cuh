@@ -15,6 +15,7 @@
 #pragma once
 #include <cstdint>
 #include "tenom_recon.cuh"
+#include "tenom_fastmath.cuh"
 
 namespace tenom {
 
@@ -37,7 +38,7 @@ constexpr int FT_FACES = 8;    /* faces per CTA along the axis, y/z sweeps (x 32
 template <int NV, int K, int AXIS>
 struct FaceTile {
   static constexpr int H = K / 2;
-  static constexpr int NC = 3 * NV + 1;  /* U[NV], F[NV], vel[NV-2], H, c, sqrt(rho) */
+  static constexpr int NC = 3 * NV + 3;  /* U[NV], F[NV], vel[NV-2], H, c, sqrt(rho), |u_a-c|, |u_a+c| */
   static constexpr int LANES = (AXIS == 0) ? 1 : 32;
   static constexpr int FACES = (AXIS == 0) ? FX_FACES : FT_FACES;
   static constexpr int ROWS = FACES + K - 1;     /* points along the axis */
@@ -46,6 +47,7 @@ struct FaceTile {
   static constexpr size_t SMEM = sizeof(double) * NC * NP;
   /* component offsets */
   static constexpr int cU = 0, cF = NV, cV = 2 * NV, cH = 3 * NV - 2, cC = 3 * NV - 1, cS = 3 * NV;
+  static constexpr int cLm = 3 * NV + 1, cLp = 3 * NV + 2;
 };
 
 __device__ __forceinline__ int bc_wrap(int j, int n, int bc) {
@@ -99,7 +101,7 @@ face_kernel(const FaceArgs A) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) u[q] = __ldg(A.U + q * A.ncell + cell);
     const double rho = u[0];
-    const double rinv = 1.0 / rho;
+    const double rinv = rcp_nr(rho);
     double vel[D], ke = 0.0;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
@@ -109,8 +111,8 @@ face_kernel(const FaceArgs A) {
     const double pr = (A.gamma - 1.0) * (u[NV - 1] - 0.5 * ke);
     const double c = sqrt(A.gamma * pr * rinv);
     const double Hh = (u[NV - 1] + pr) * rinv;
-    if (!(rho > 0.0)) st |= ST_RHO;
-    if (!(pr > 0.0)) st |= ST_P;
+    if (!ipos(rho)) st |= ST_RHO;
+    if (!ipos(pr)) st |= ST_P;
     const double un = vel[AXIS];
 #pragma unroll
     for (int q = 0; q < NV; ++q) sm[(T::cU + q) * T::NP + p] = u[q];
@@ -123,6 +125,8 @@ face_kernel(const FaceArgs A) {
     sm[T::cH * T::NP + p] = Hh;
     sm[T::cC * T::NP + p] = c;
     sm[T::cS * T::NP + p] = sqrt(rho);
+    sm[T::cLm * T::NP + p] = iabs(un - c);
+    sm[T::cLp * T::NP + p] = iabs(un + c);
   }
   __syncthreads();
 
@@ -138,7 +142,7 @@ face_kernel(const FaceArgs A) {
     };
     /* Roe average of cells f-1 (point H-1) and f (point H) */
     const double sL = P(T::cS, H - 1), sR = P(T::cS, H);
-    const double wsum = 1.0 / (sL + sR);
+    const double wsum = rcp_nr(sL + sR);
     double ut[D], q2 = 0.0;
 #pragma unroll
     for (int d = 0; d < D; ++d) {
@@ -147,12 +151,20 @@ face_kernel(const FaceArgs A) {
     }
     const double Ht = (sL * P(T::cH, H - 1) + sR * P(T::cH, H)) * wsum;
     const double c2 = (A.gamma - 1.0) * (Ht - 0.5 * q2);
-    if (!(c2 > 0.0)) st |= ST_ROE;
-    const double ct = sqrt(c2);
-    const double cinv = 1.0 / ct;
-    const double b1 = (A.gamma - 1.0) / c2;
+    if (!ipos(c2)) st |= ST_ROE;
+    const double cinv = rsqrt_nr(c2);
+    const double ct = c2 * cinv;
+    const double b1 = (A.gamma - 1.0) * (cinv * cinv);
     const double b2 = 0.5 * q2 * b1;
     const double una = ut[AXIS];
+    /* LLF: alpha_s = max over the K stencil points of |lambda_s|, one per eigenvalue family */
+    double a_m = 0.0, a_0 = 0.0, a_p = 0.0;
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      a_m = imax_nonneg(a_m, P(T::cLm, q));
+      a_0 = imax_nonneg(a_0, iabs(P(T::cV + AXIS, q)));
+      a_p = imax_nonneg(a_p, P(T::cLp, q));
+    }
 
     double Fh[NV];
 #pragma unroll
@@ -189,29 +201,32 @@ face_kernel(const FaceArgs A) {
         for (int d = 0; d < D; ++d) l[1 + d] = (d == dt) ? 1.0 : 0.0;
         l[NV - 1] = 0.0;
       }
-      /* project the K stencil points; LLF alpha_s = max_m |lambda_s(U_m)| */
+      /* characteristic projection of the K stencil points and LLF split
+         g+- = (G +- alpha W)/2, evaluated as fma(+-alpha/2, W, G/2) */
+      const double ha = 0.5 * ((s == 0) ? a_m : (s == NV - 1 ? a_p : a_0));
       double gp[K], gm[K];
-      double alpha = 0.0;
+      if (acoustic || s == 1) {
 #pragma unroll
-      for (int q = 0; q < K; ++q) {
-        double w = 0.0, g = 0.0;
+        for (int q = 0; q < K; ++q) {
+          double w = l[0] * P(T::cU, q), g = l[0] * P(T::cF, q);
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          w += l[v] * P(T::cU + v, q);
-          g += l[v] * P(T::cF + v, q);
+          for (int v = 1; v < NV; ++v) {
+            w = fma(l[v], P(T::cU + v, q), w);
+            g = fma(l[v], P(T::cF + v, q), g);
+          }
+          const double hg = 0.5 * g;
+          gp[q] = fma(ha, w, hg);
+          gm[q] = fma(-ha, w, hg);
         }
-        const double un = P(T::cV + AXIS, q);
-        const double cq = P(T::cC, q);
-        const double lam = (s == 0) ? un - cq : (s == NV - 1 ? un + cq : un);
-        alpha = (q == 0) ? fabs(lam) : dmax(alpha, fabs(lam));
-        gp[q] = w;  /* hold W, G until alpha is known */
-        gm[q] = g;
-      }
+      } else {
+        /* shear wave: l = (-u_t, e_t, 0) */
 #pragma unroll
-      for (int q = 0; q < K; ++q) {
-        const double w = gp[q], g = gm[q];
-        gp[q] = 0.5 * (g + alpha * w);
-        gm[q] = 0.5 * (g - alpha * w);
+        for (int q = 0; q < K; ++q) {
+          const double w = fma(-utt, P(T::cU, q), P(T::cU + 1 + dt, q));
+          const double hg = 0.5 * fma(-utt, P(T::cF, q), P(T::cF + 1 + dt, q));
+          gp[q] = fma(ha, w, hg);
+          gm[q] = fma(-ha, w, hg);
+        }
       }
       /* f+ on the upwind stencil, f- on the stencil mirrored about x_{i+1/2} */
       double vm[K];

@@ -12,10 +12,15 @@
  *   assembly with constant weights w_k = d_k (Eq. reconstuction, Section 3.3).
  * The indicators use exact sum-of-squares forms over the differences D_t = v[t+1] - v[t]
  * (teno_coeffs.cuh); the TVD5 flux is evaluated in its division-free difference form.
+ * FP64 is the scarce resource on GB300: the cutoff compares gamma_k with C_T * sum gamma
+ * (same truth value as chi_k < C_T, no division), 1/(beta_k + eps) is a Newton-Raphson
+ * reciprocal, and every comparison, min/max and minmod runs on the integer pipe
+ * (tenom_fastmath.cuh).
  */
 #pragma once
 #include <cstdint>
 #include "teno_coeffs.cuh"
+#include "tenom_fastmath.cuh"
 
 namespace tenom {
 
@@ -36,20 +41,20 @@ struct SchemeDev {
   double d[6];
 };
 
-__device__ __forceinline__ double dmin(double a, double b) { return b < a ? b : a; }
-__device__ __forceinline__ double dmax(double a, double b) { return a < b ? b : a; }
+__device__ __forceinline__ double dmin(double a, double b) { return imin(a, b); }
+__device__ __forceinline__ double dmax(double a, double b) { return imax(a, b); }
 
 /* minmod of two arguments (Eq. minmod222; zero if an argument is zero). */
 __device__ __forceinline__ double minmod2(double x, double y) {
-  if (x > 0.0 && y > 0.0) return dmin(x, y);
-  if (x < 0.0 && y < 0.0) return dmax(x, y);
+  if (ipos(x) && ipos(y)) return imin(x, y);
+  if (ineg(x) && ineg(y)) return imax(x, y);
   return 0.0;
 }
 
 /* minmod of four arguments (Eq. minmod444). */
 __device__ __forceinline__ double minmod4(double a, double b, double c, double d) {
-  if (a > 0.0 && b > 0.0 && c > 0.0 && d > 0.0) return dmin(dmin(a, b), dmin(c, d));
-  if (a < 0.0 && b < 0.0 && c < 0.0 && d < 0.0) return dmax(dmax(a, b), dmax(c, d));
+  if (ipos(a) && ipos(b) && ipos(c) && ipos(d)) return imin(imin(a, b), imin(c, d));
+  if (ineg(a) && ineg(b) && ineg(c) && ineg(d)) return imax(imax(a, b), imax(c, d));
   return 0.0;
 }
 
@@ -74,8 +79,8 @@ __device__ __forceinline__ void mp_bounds(const double* v, const SchemeDev& S, d
   const double f_ul = fi + S.mp_alpha * (fi - fim);          /* Eq. upper_limiter */
   const double f_md = 0.5 * (fi + fip) - 0.5 * dhp;          /* Eq. median_value */
   const double f_lc = fi + 0.5 * (fi - fim) + S.mp_beta_third * dhm;  /* Eq. large_curvature */
-  fmin = dmax(dmin(dmin(fi, fip), f_md), dmin(dmin(fi, f_ul), f_lc));
-  fmax = dmin(dmax(dmax(fi, fip), f_md), dmax(dmax(fi, f_ul), f_lc));
+  fmin = imax(imin(imin(fi, fip), f_md), imin(imin(fi, f_ul), f_lc));
+  fmax = imin(imax(imax(fi, fip), f_md), imax(imax(fi, f_ul), f_lc));
 }
 
 /* TVD5 flux f_i + phi delta^-/2 in difference form: with D_m = f_m - f_{m-1} and
@@ -84,10 +89,10 @@ __device__ __forceinline__ void mp_bounds(const double* v, const SchemeDev& S, d
 template <int c>
 __device__ __forceinline__ double tvd5_flux(const double* v) {
   const double Dm = v[c - 1] - v[c - 2], D0 = v[c] - v[c - 1], Dp = v[c + 1] - v[c], Dpp = v[c + 2] - v[c + 1];
-  const double B = (-2.0 * Dm + 11.0 * D0 + 24.0 * Dp - 3.0 * Dpp) / 30.0;
+  const double B = (-2.0 * Dm + 11.0 * D0 + 24.0 * Dp - 3.0 * Dpp) * (1.0 / 30.0);
   double pd = 0.0;
-  if (D0 > 0.0) pd = dmax(0.0, dmin(dmin(2.0 * D0, 2.0 * Dp), B));
-  else if (D0 < 0.0) pd = dmin(0.0, dmax(dmax(2.0 * D0, 2.0 * Dp), B));
+  if (ipos(D0)) pd = imax(0.0, imin(imin(2.0 * D0, 2.0 * Dp), B));
+  else if (ineg(D0)) pd = imin(0.0, imax(imax(2.0 * D0, 2.0 * Dp), B));
   return v[c] + 0.5 * pd;
 }
 
@@ -111,10 +116,10 @@ __device__ __forceinline__ double adaptive_ct(const double* D, int* e) {
   for (int q = 0; q < 4; ++q) {
     /* eta_{i-1+q}: Delta f_{j+1/2} = D[c + j], Delta f_{j-1/2} = D[c + j - 1] with j = q - 1 */
     const double dfp = D[c + q - 1], dfm = D[c + q - 2];
-    const double eta = (fabs(2.0 * dfp * dfm) + eps) / (dfp * dfp + dfm * dfm + eps);
-    eh = (q == 0) ? eta : dmin(eh, eta);
+    const double eta = (iabs(2.0 * dfp * dfm) + eps) * rcp_nr(dfp * dfp + dfm * dfm + eps);
+    eh = (q == 0) ? eta : imin(eh, eta);
   }
-  const double m = 1.0 - dmin(1.0, eh / Cr);
+  const double m = 1.0 - imin(1.0, eh * (1.0 / Cr));
   const double om = 1.0 - m;
   const double g = om * om * om * om * (1.0 + 4.0 * m);
   const double beta = a1 - a2 * (1.0 - g);
@@ -152,11 +157,11 @@ __device__ __forceinline__ double teno_m(const double (&v)[K], const SchemeDev& 
   } else {
     bK = betaK6<0>(D);
   }
-  const double tau = fabs(bK - (bk[1] + bk[2] + 4.0 * bk[0]) / 6.0);
+  const double tau = iabs(bK - (bk[1] + bk[2] + 4.0 * bk[0]) * (1.0 / 6.0));
   double gk[nk], sum = 0.0;
 #pragma unroll
   for (int k = 0; k < nk; ++k) {
-    const double x = 1.0 + tau / (bk[k] + 1e-40);
+    const double x = fma(tau, rcp_nr(bk[k] + 1e-40), 1.0);
     const double x3 = x * x * x;
     gk[k] = x3 * x3;
     sum += gk[k];
@@ -164,10 +169,12 @@ __device__ __forceinline__ double teno_m(const double (&v)[K], const SchemeDev& 
   double CT = S.ct_const;
   int ex = 7;
   if (S.ct_mode == CT_ADAPTIVE) CT = adaptive_ct<c>(D, &ex);
+  /* chi_k < C_T  <=>  gamma_k < C_T sum gamma (all positive: compared as bit patterns) */
+  const double thr = CT * sum;
   unsigned bits = 0;
 #pragma unroll
-  for (int k = 0; k < nk; ++k) bits |= (gk[k] / sum < CT ? 0u : 1u) << k;
-  if (!isfinite(sum)) st |= ST_NONFINITE;
+  for (int k = 0; k < nk; ++k) bits |= (ilt_nonneg(gk[k], thr) ? 0u : 1u) << k;
+  if (dbits(sum) >= 0x7ff0000000000000ll) st |= ST_NONFINITE;
   flag = bits | ((unsigned)((ex - 7) & 3) << 6);
   if (S.weights == W_TENO) {
     double num = 0.0, den = 0.0;

@@ -66,6 +66,8 @@ def lib():
         L.tenom_last_error.restype = ctypes.c_char_p
         L.tenom_kernel_timing.argtypes = [VP, c_int, P(c_double), P(ctypes.c_longlong)]
         L.tenom_fp64_peak.argtypes = [VP, c_int, c_int, P(c_double)]
+        L.tenom_check_fastmath.argtypes = [VP, VP, ctypes.c_longlong, VP]
+        L.tenom_check_fastmath.restype = c_int
         L.tenom_rhs_noalloc.argtypes = [P(tenom_grid), P(tenom_scheme), VP, VP, VP, VP]
         L.tenom_rhs_noalloc.restype = c_int
         for name in ("tenom_scheme_default", "tenom_create", "tenom_destroy", "tenom_init_state", "tenom_rhs",
