@@ -29,6 +29,10 @@ WORKLOADS = {
     "broadband_2d_2048_teno8_tvd5": ("broadband_2d", (2048, 2048), 8, 1),
     "solenoidal_3d_256_teno8_mp": ("solenoidal_3d", (256, 256, 256), 8, 0),
 }
+BATCH_WORKLOADS = {
+    # name: (problems, seed, nmin, nmax, K, limiter)
+    "batched_riemann_512_teno6_mp": (512, 4, 128, 8192, 6, 0),
+}
 DEFAULT = "broadband_2d_2048_teno6_mp"
 FP64_NOMINAL = 1.25e12  # FLOP/s, GB300 FP64 (an FMA counts 2)
 
@@ -37,7 +41,8 @@ def flops_per_face(name):
     """Stored algorithmic FP64 operation counts per face (oracle op counter)."""
     key = {"broadband_2d_2048_teno6_mp": ("broadband_2d_2048", "K=6", "lim=MP"),
            "broadband_2d_2048_teno8_tvd5": ("broadband_2d_2048", "K=8", "lim=TVD5"),
-           "solenoidal_3d_256_teno8_mp": ("solenoidal_3d_256", "K=8", "lim=MP")}[name]
+           "solenoidal_3d_256_teno8_mp": ("solenoidal_3d_256", "K=8", "lim=MP"),
+           "batched_riemann_512_teno6_mp": ("riemann_1d_batch", "K=6", "lim=MP")}[name]
     with open(os.path.join(ROOT, "tests", "golden", "flops_per_face.txt")) as fh:
         for line in fh:
             parts = line.split()
@@ -157,11 +162,56 @@ def oracle_rate(name, seconds=12.0, seed=2):
     return nc / el, sample, el
 
 
+def oracle_rate_batch(name, seconds):
+    """CPU oracle (single thread): operator evaluations of the batch's problems, in order,
+    until about `seconds` of work; returns (cell-updates/s per stage, sample, elapsed s)."""
+    import oracle as orc
+    from paper_2010_13289_gb300 import problems as PB
+    nprob, seed, nmin, nmax, K, lim = BATCH_WORKLOADS[name]
+    if name not in _PRIM_CACHE:
+        _PRIM_CACHE[name] = PB.batch_riemann(nprob, seed, nmin, nmax)
+    sizes, prims, dxs = _PRIM_CACHE[name]
+    S = orc.make_scheme(K, limiter=lim)
+    cells, el, used = 0, 0.0, 0
+    for n, p, dx in zip(sizes, prims, dxs):
+        g = orc.make_grid((int(n),), (dx,), (orc.BC_TRANSMISSIVE,))
+        U = orc.init_state(g, p)
+        t0 = time.perf_counter()
+        orc.rhs(g, S, U)
+        el += time.perf_counter() - t0
+        cells += int(n)
+        used += 1
+        if el >= seconds:
+            break
+    return cells / el, "operator evaluations of the first %d of the %d batch problems (%d cells), 1 thread" % (
+        used, nprob, cells), el
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     name = args.workload
+    if name in BATCH_WORKLOADS:
+        per_step = args.ref_seconds if args.ref_seconds else max(1.0, min(12.0, 150.0 / (args.steps + args.warmup)))
+        for _ in range(args.warmup):
+            oracle_rate_batch(name, min(1.0, per_step))
+        rates, times = [], []
+        for _ in range(args.steps):
+            r, sample, el = oracle_rate_batch(name, per_step)
+            rates.append(r)
+            times.append(el)
+        v = statistics.median(rates)
+        nprob, seed, nmin, nmax, K, lim = BATCH_WORKLOADS[name]
+        out = {"impl": "reference", "metric": "cell-updates/s per RK stage (FP64)", "value": v,
+               "unit": "cell-updates/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded, shaped like the paper's workloads)",
+               "config": {"workload": name, "problems": nprob, "K": K, "limiter": "MP" if lim == 0 else "TVD5"},
+               "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+               "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out), flush=True)
+        return
     per_step = args.ref_seconds if args.ref_seconds else max(1.0, min(12.0, 150.0 / (args.steps + args.warmup)))
     rates, samples, times = [], None, []
     for _ in range(args.warmup):
@@ -289,13 +339,150 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_batch(args):
+    """Batched workload: 512 independent seeded 1D Riemann problems, sizes log-uniform
+    128..8192, one persistent launch per RK stage, a CUDA graph per RK step, autotuned tiles;
+    compared with advancing the same problems by separate plain launches (one context each)."""
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2010_13289_gb300 import problems as PB
+    from paper_2010_13289_gb300 import tenom as T
+    name = args.workload
+    nprob, seed, nmin, nmax, K, lim = BATCH_WORKLOADS[name]
+    sizes, prims, dxs = PB.batch_riemann(nprob, seed + rank, nmin, nmax)
+    B = T.Batch(sizes, dxs, T.make_scheme(K, limiter=lim))
+    prim = np.zeros((3, B.total))
+    for j in range(nprob):
+        prim[:, B.off[j]:B.off[j + 1]] = prims[j]
+    U = B.init_state(torch.from_numpy(prim).cuda())
+    U0 = U.clone()
+    tile, ctas = B.autotune(U)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    B.step(U, nsteps=args.warmup)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    B.step(U, nsteps=args.steps)
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = t.item()
+    assert B.status() == 0
+    value = float(B.total) * 3 * args.steps * ws / (ms * 1e-3)
+
+    # the same problems advanced by separate plain launches (one context per problem)
+    sep_steps = max(1, min(args.steps, 3))
+    solvers, Us = [], []
+    for n, p, dx in zip(sizes, prims, dxs):
+        S = T.Solver((int(n),), (dx,), (T.BC_TRANSMISSIVE,), T.make_scheme(K, limiter=lim))
+        solvers.append(S)
+        Us.append(S.init_state(torch.from_numpy(p).cuda()))
+    for S, u in zip(solvers, Us):
+        S.advance(u, 1)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(sep_steps):
+        for S, u in zip(solvers, Us):
+            S.advance(u, 1)
+    e1.record(stream)
+    barrier()
+    sep_ms = e0.elapsed_time(e1)
+    sep_value = float(B.total) * 3 * sep_steps / (sep_ms * 1e-3)
+    for S in solvers:
+        S.close()
+
+    # stage-kernel time: persistent stage-1 launches with CUDA events (dt from the last step)
+    lib = T.lib()
+    import ctypes
+    reps = 10
+    k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k0.record(stream)
+    for _ in range(reps):
+        lib.tenom_batch_stage(B._b, 1, ctypes.c_void_p(U.data_ptr()))
+    k1.record(stream)
+    barrier()
+    stage_ms = k0.elapsed_time(k1) / reps
+
+    # end to end: host state in pinned memory -> device, one graph step, device -> host
+    host_in = torch.empty((3, B.total), dtype=torch.float64, pin_memory=True)
+    host_out = torch.empty_like(host_in)
+    host_in.copy_(U0.cpu())
+    Ue = torch.empty_like(U)
+    e2e_steps = max(1, min(args.steps, 5))
+    B.step(Ue.copy_(host_in, non_blocking=True), nsteps=1)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        Ue.copy_(host_in, non_blocking=True)
+        B.step(Ue, nsteps=1)
+        host_out.copy_(Ue, non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e = float(B.total) * 3 * e2e_steps * ws / e2e_s
+    state_bytes = 8 * 3 * B.total
+
+    fpf = flops_per_face(name)
+    faces = float(np.sum(sizes + 1))
+    achieved = fpf * faces / (stage_ms * 1e-3)
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL, "unit": "FLOP/s",
+            "frac": achieved / FP64_NOMINAL, "traffic": None,
+            "kernel": "batch_stage_kernel (persistent faces + flux difference + stage combine)",
+            "flops_per_face": fpf, "faces_per_launch": faces, "ms_per_launch": stage_ms,
+            "peak_note": "nominal GB300 FP64 (FMA = 2 flops)"}
+    out = {"metric": "cell-updates/s per RK stage (FP64)", "value": value, "unit": "cell-updates/s",
+           "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded, shaped like the paper's workloads)",
+           "config": {"workload": name, "problems": nprob, "cells": int(B.total), "K": K,
+                      "limiter": "MP" if lim == 0 else "TVD5", "tile": tile, "ctas_per_sm": ctas,
+                      "launch": "persistent stage kernel per RK stage, CUDA graph per step",
+                      "parallelism": "replicas" if ws > 1 else "single",
+                      "l2": "state + 2 stage buffers: %.0f MB" % (3 * state_bytes / 1e6)},
+           "separate_launches": {"value": sep_value, "unit": "cell-updates/s", "steps": sep_steps,
+                                 "speedup_of_batched": value / sep_value},
+           "e2e": {"value": e2e, "unit": "cell-updates/s", "h2d_bytes_per_step": state_bytes,
+                   "d2h_bytes_per_step": state_bytes},
+           "gpu_launches": 6 * args.steps, "roofline": roof, "clocks": clk}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        r, sample, el = oracle_rate_batch(name, args.ref_seconds or 10.0)
+        out["cpu_baseline"] = {"value": r, "unit": "cell-updates/s", "cores": 1, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    B.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS))
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--ref-seconds", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -304,6 +491,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload in BATCH_WORKLOADS:
+        run_batch(args)
     else:
         run_ours(args)
 

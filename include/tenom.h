@@ -127,6 +127,41 @@ tenom_status tenom_advance_host(tenom_ctx* ctx, const double* U_host_in, double*
  * [beta] - 7 of Eq. cut-off_adjust when C_T is adaptive.  flags may be NULL. */
 tenom_status tenom_face_dump(tenom_ctx* ctx, const double* U, int axis, double* Fhat, uint8_t* flags);
 
+/* ---------------------------------------------------------------- batched 1D problems
+ * Many independent 1D Euler problems of uneven size advanced together (each problem as in
+ * tenom_advance, on its own grid, time and CFL step).  State: one caller-owned device array
+ * U[3][total] where problem j owns cells [off_j, off_j + n_j) (tenom_batch_layout).  Each RK
+ * stage is one persistent kernel over a work list of (problem, face tile) items; a step is
+ * captured once into a CUDA graph and replayed.  Problems whose time reached their t_end
+ * are masked (their state is left untouched). */
+typedef struct tenom_batch tenom_batch;
+
+/* n[j], dx[j] (host arrays of nprob); bc[j] per problem (host, NULL = all transmissive);
+ * scheme as for tenom_create (K = 6 or 8; MP or TVD5).  t_j = 0, t_end_j = +inf. */
+tenom_status tenom_batch_create(tenom_batch** b, int nprob, const int* n, const double* dx, const int* bc,
+                                double gamma, const tenom_scheme* scheme, void* stream);
+tenom_status tenom_batch_destroy(tenom_batch* b);
+/* off_host[nprob + 1] cell offsets and the total cell count. */
+tenom_status tenom_batch_layout(const tenom_batch* b, long long* off_host, long long* total);
+/* U = conserved state of prim (rho, u, p), both [3][total] device arrays. */
+tenom_status tenom_batch_init_state(tenom_batch* b, const double* prim, double* U);
+/* Set t_j and/or t_end_j from host arrays (NULL leaves them); synchronises. */
+tenom_status tenom_batch_set_time(tenom_batch* b, const double* t_host, const double* t_end_host);
+tenom_status tenom_batch_get_time(tenom_batch* b, double* t_host);
+tenom_status tenom_batch_status_word(tenom_batch* b, int* status_host, int reset);
+/* nsteps SSP-RK3 steps of every unfinished problem: per problem dt_j = min(cfl / max signal
+ * speed_j, t_end_j - t_j); replays a CUDA graph of one step (rebuilt when U or cfl change). */
+tenom_status tenom_batch_step(tenom_batch* b, double* U, double cfl, int nsteps);
+/* The same step sequence launched directly on the stream (no graph). */
+tenom_status tenom_batch_step_direct(tenom_batch* b, double* U, double cfl, int nsteps);
+/* One persistent stage launch (1, 2, 3) with the current per-problem dt: stage 1 reads U and
+ * writes the stage buffer, stage 3 writes U.  For drivers that sequence stages themselves. */
+tenom_status tenom_batch_stage(tenom_batch* b, int stage, double* U);
+/* Time the stage kernel for tiles of 64/128/256 faces and 1/2/4/8 resident CTAs per SM on
+ * this batch and keep the fastest (writes the choice if the pointers are non-NULL). */
+tenom_status tenom_batch_autotune(tenom_batch* b, double* U, int* tile, int* ctas_per_sm);
+tenom_status tenom_batch_set_tiling(tenom_batch* b, int tile, int ctas_per_sm);
+
 /* Size of the static device scratch of tenom_rhs_noalloc: 16 MiB, held on every GPU that
  * loads this library until the process exits. */
 #define TENOM_NOALLOC_SCRATCH_BYTES (16u << 20)

@@ -69,6 +69,23 @@ def lib():
         L.tenom_check_fastmath.argtypes = [VP, VP, ctypes.c_longlong, VP]
         L.tenom_check_fastmath.restype = c_int
         L.tenom_rhs_noalloc.argtypes = [P(tenom_grid), P(tenom_scheme), VP, VP, VP, VP]
+        L.tenom_batch_create.argtypes = [P(VP), c_int, VP, VP, VP, c_double, P(tenom_scheme), VP]
+        L.tenom_batch_destroy.argtypes = [VP]
+        L.tenom_batch_layout.argtypes = [VP, VP, P(ctypes.c_longlong)]
+        L.tenom_batch_init_state.argtypes = [VP, VP, VP]
+        L.tenom_batch_set_time.argtypes = [VP, VP, VP]
+        L.tenom_batch_get_time.argtypes = [VP, VP]
+        L.tenom_batch_status_word.argtypes = [VP, P(c_int), c_int]
+        L.tenom_batch_step.argtypes = [VP, VP, c_double, c_int]
+        L.tenom_batch_step_direct.argtypes = [VP, VP, c_double, c_int]
+        L.tenom_batch_stage.argtypes = [VP, c_int, VP]
+        L.tenom_batch_autotune.argtypes = [VP, VP, P(c_int), P(c_int)]
+        L.tenom_batch_set_tiling.argtypes = [VP, c_int, c_int]
+        for name in ("tenom_batch_create", "tenom_batch_destroy", "tenom_batch_layout", "tenom_batch_init_state",
+                     "tenom_batch_set_time", "tenom_batch_get_time", "tenom_batch_status_word", "tenom_batch_step",
+                     "tenom_batch_step_direct", "tenom_batch_stage", "tenom_batch_autotune",
+                     "tenom_batch_set_tiling"):
+            getattr(L, name).restype = c_int
         L.tenom_rhs_noalloc.restype = c_int
         for name in ("tenom_scheme_default", "tenom_create", "tenom_destroy", "tenom_init_state", "tenom_rhs",
                      "tenom_max_dt", "tenom_rk3_step", "tenom_advance", "tenom_advance_host", "tenom_face_dump",
@@ -247,3 +264,86 @@ def fp64_peak(nblocks=152 * 8, iters=4096):
     if st != TENOM_OK:
         raise TenomError(st, "tenom_fp64_peak")
     return f.value
+
+
+class Batch:
+    """Independent 1D problems of uneven size advanced together (tenom_batch_*).
+
+    State tensors are float64 CUDA tensors of shape (3, total): problem j owns columns
+    off[j]:off[j+1]."""
+
+    def __init__(self, n, dx, scheme=None, bc=None, gamma=1.4, stream=None):
+        import torch
+        self.n = np.ascontiguousarray(n, dtype=np.int32)
+        self.dx = np.ascontiguousarray(dx, dtype=np.float64)
+        self.P = int(self.n.size)
+        self.scheme = scheme if scheme is not None else make_scheme(6)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self._b = ctypes.c_void_p()
+        bca = None if bc is None else np.ascontiguousarray(bc, dtype=np.int32)
+        st = lib().tenom_batch_create(ctypes.byref(self._b), self.P, ctypes.c_void_p(self.n.ctypes.data),
+                                      ctypes.c_void_p(self.dx.ctypes.data),
+                                      None if bca is None else ctypes.c_void_p(bca.ctypes.data), gamma,
+                                      ctypes.byref(self.scheme), ctypes.c_void_p(self.stream.cuda_stream))
+        if st != TENOM_OK:
+            raise TenomError(st, "tenom_batch_create")
+        self._bc_keep = bca
+        self.off = np.zeros(self.P + 1, dtype=np.int64)
+        tot = ctypes.c_longlong(0)
+        self._check(lib().tenom_batch_layout(self._b, ctypes.c_void_p(self.off.ctypes.data), ctypes.byref(tot)),
+                    "layout")
+        self.total = int(tot.value)
+
+    def _check(self, st, what):
+        if st != TENOM_OK:
+            raise TenomError(st, "tenom_batch " + what)
+
+    def close(self):
+        if self._b:
+            lib().tenom_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_state(self, prim):
+        import torch
+        U = torch.empty((3, self.total), dtype=torch.float64, device="cuda")
+        self._check(lib().tenom_batch_init_state(self._b, _ptr(prim), _ptr(U)), "init_state")
+        return U
+
+    def set_time(self, t=None, t_end=None):
+        ta = None if t is None else np.ascontiguousarray(np.broadcast_to(t, (self.P,)), dtype=np.float64)
+        te = None if t_end is None else np.ascontiguousarray(np.broadcast_to(t_end, (self.P,)), dtype=np.float64)
+        self._check(lib().tenom_batch_set_time(self._b, None if ta is None else ctypes.c_void_p(ta.ctypes.data),
+                                               None if te is None else ctypes.c_void_p(te.ctypes.data)),
+                    "set_time")
+
+    def times(self):
+        t = np.zeros(self.P)
+        self._check(lib().tenom_batch_get_time(self._b, ctypes.c_void_p(t.ctypes.data)), "get_time")
+        return t
+
+    def step(self, U, nsteps=1, cfl=0.4, graph=True):
+        fn = lib().tenom_batch_step if graph else lib().tenom_batch_step_direct
+        self._check(fn(self._b, _ptr(U), cfl, nsteps), "step")
+        return U
+
+    def autotune(self, U):
+        t, c = ctypes.c_int(0), ctypes.c_int(0)
+        self._check(lib().tenom_batch_autotune(self._b, _ptr(U), ctypes.byref(t), ctypes.byref(c)), "autotune")
+        return t.value, c.value
+
+    def set_tiling(self, tile, ctas_per_sm):
+        self._check(lib().tenom_batch_set_tiling(self._b, tile, ctas_per_sm), "set_tiling")
+
+    def status(self, reset=False):
+        v = ctypes.c_int(0)
+        st = lib().tenom_batch_status_word(self._b, ctypes.byref(v), 1 if reset else 0)
+        if st not in (TENOM_OK, TENOM_E_NONPHYSICAL):
+            self._check(st, "status_word")
+        return v.value
+
