@@ -188,6 +188,34 @@ tenom_status tenom_batch_set_tiling(tenom_batch* b, int tile, int ctas_per_sm);
 tenom_status tenom_rhs_noalloc(const tenom_grid* grid, const tenom_scheme* scheme, const double* U, double* dUdt,
                                int* status_dev, void* stream);
 
+/* ---------------------------------------------------------------- frozen-branch adjoint
+ * Reverse-mode derivative of the solver with every branch fixed at the forward pass: the
+ * cutoff flags delta_k (Eq. cut-off), the limiter selections (MP median / bounds, TVD5 slope),
+ * the argmax of the LLF alpha and dt.  Because TENO-M assembles with constant weights
+ * w_k = d_k (Section 3.3), no derivative flows through beta, tau, gamma or chi.  All arrays
+ * are device [nvar][ncell] unless stated. */
+
+/* Bytes of cutoff flags one stage records (all axes): sum_a nface_a * nvar * 2. */
+size_t tenom_flags_bytes(const tenom_ctx* ctx);
+
+/* Ubar = L'(U)^T w (vector-Jacobian product of tenom_rhs at U; flags decided at U). */
+tenom_status tenom_rhs_vjp(tenom_ctx* ctx, const double* U, const double* w, double* Ubar);
+
+/* tenom_rk3_step that also records the tape of the step: tape_states = [U1, U2] (2 * nvar *
+ * ncell doubles) and tape_flags (3 * tenom_flags_bytes bytes), for tenom_rk3_step_adjoint_tape. */
+tenom_status tenom_rk3_step_record(tenom_ctx* ctx, double* U, const double* dt_dev, double* tape_states,
+                                   uint8_t* tape_flags);
+
+/* Ubar_n = (dU^{n+1}/dU^n)^T Ubar_np1 for the step recorded from U_n (dt frozen).  Ubar_n
+ * and Ubar_np1 must be distinct arrays. */
+tenom_status tenom_rk3_step_adjoint_tape(tenom_ctx* ctx, const double* U_n, const double* tape_states,
+                                         const uint8_t* tape_flags, const double* dt_dev, const double* Ubar_np1,
+                                         double* Ubar_n);
+
+/* The same without a caller tape: records the step from U_n internally first. */
+tenom_status tenom_rk3_step_adjoint(tenom_ctx* ctx, const double* U_n, const double* dt_dev, const double* Ubar_np1,
+                                    double* Ubar_n);
+
 /* Sticky device status word (TENOM_ST_* bits); synchronises the stream.  reset != 0 clears it. */
 tenom_status tenom_status_word(tenom_ctx* ctx, int* status_host, int reset);
 

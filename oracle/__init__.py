@@ -108,6 +108,8 @@ def lib():
         L.orc_rk3_step.restype = c_int
         L.orc_advance.argtypes = [gp, sp, dp, c_double, c_double, c_int, dp, ip]
         L.orc_advance.restype = c_int
+        L.orc_rhs_jvp.argtypes = [gp, sp, dp, dp, dp, dp]
+        L.orc_rhs_jvp.restype = c_int
         L.orc_rk3_step_jvp.argtypes = [gp, sp, dp, dp, c_double]
         L.orc_rk3_step_jvp.restype = c_int
         L.orc_face_flops.argtypes = [gp, sp, dp, c_int]
@@ -254,6 +256,16 @@ def rk3_step_jvp(grid, scheme, U, dU, dt):
     dU = _c(dU).copy()
     bad = lib().orc_rk3_step_jvp(ctypes.byref(grid), ctypes.byref(scheme), _d(U), _d(dU), dt)
     return U, dU, bad
+
+
+def rhs_jvp(grid, scheme, U, dU):
+    """(L(U), L'(U) dU) with every branch frozen at U (dual numbers)."""
+    U = _c(U)
+    dU = _c(dU)
+    Lv = np.zeros_like(U)
+    dL = np.zeros_like(U)
+    bad = lib().orc_rhs_jvp(ctypes.byref(grid), ctypes.byref(scheme), _d(U), _d(dU), _d(Lv), _d(dL))
+    return Lv, dL, bad
 
 
 def face_flops(grid, scheme, U, axis):

@@ -155,6 +155,18 @@ int orc_rk3_step_jvp(const Grid* g, const Scheme* s, double* U, double* dU, doub
   return bad;
 }
 
+/* Forward-mode derivative of the operator L at U in direction dU (branches frozen). */
+int orc_rhs_jvp(const Grid* g, const Scheme* s, const double* U, const double* dU, double* L, double* dL) {
+  Grid G = norm_grid(g);
+  Scheme S = norm_scheme(s);
+  long long N = (G.dim + 2) * ncell(G);
+  std::vector<Dual> X(N), Y(N);
+  for (long long q = 0; q < N; ++q) X[q] = Dual(U[q], dU[q]);
+  int bad = rhs<Dual>(G, S, X.data(), Y.data());
+  for (long long q = 0; q < N; ++q) { L[q] = Y[q].v; dL[q] = Y[q].d; }
+  return bad;
+}
+
 /* Counted FP64 operations of all faces of one axis (+,-,*,/,sqrt, compare/min/max/abs). */
 long long orc_face_flops(const Grid* g, const Scheme* s, const double* U, int axis) {
   Grid G = norm_grid(g);

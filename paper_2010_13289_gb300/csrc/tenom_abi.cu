@@ -10,6 +10,7 @@
 
 #include "tenom.h"
 #include "tenom_internal.h"
+#include "tenom_adjoint_kernels.cuh"
 
 namespace tenom {
 
@@ -172,6 +173,19 @@ __global__ void fastmath_check_kernel(const double* x, double* out, long long n)
   }
 }
 
+/* out = c0 x0 + c1 x1 + c2 x2 + c3 dt x3 (null operands skipped; dt read on the device) */
+__global__ void lincomb_kernel(long long n, double* out, double c0, const double* x0, double c1, const double* x1,
+                               double c2, const double* x2, double c3, const double* dtp, const double* x3) {
+  const double dt = dtp ? *dtp : 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    double r = c0 * x0[i];
+    if (x1) r += c1 * x1[i];
+    if (x2) r += c2 * x2[i];
+    if (x3) r += (c3 * dt) * x3[i];
+    out[i] = r;
+  }
+}
+
 /* FP64 pipe probe: 8 independent FMA chains per thread. */
 __global__ void dfma_probe_kernel(int iters, double a, double b, double* sink) {
   double x[8];
@@ -205,6 +219,8 @@ struct tenom_ctx {
   double* dt;          /* device dt */
   double* tbuf;        /* device scratch time */
   double* Uhost;       /* device state for tenom_advance_host (allocated on first use) */
+  double* adj;         /* adjoint workspace: A1, A2, A3, Z, then an internal tape (U^n copy, U1, U2) */
+  uint8_t* adj_flags;  /* internal tape flags (3 stages) */
   unsigned long long* smax;
   int* status;
   std::string err;
@@ -315,6 +331,8 @@ tenom_status tenom_create(tenom_ctx** out, const tenom_grid* grid, const tenom_s
     if (a < grid->dim) c->nface[a] = c->ncell / grid->n[a] * (grid->n[a] + 1);
   }
   c->Uhost = nullptr;
+  c->adj = nullptr;
+  c->adj_flags = nullptr;
   c->timing = false;
   c->ev_used = 0;
   c->face_ms = 0;
@@ -346,6 +364,8 @@ tenom_status tenom_destroy(tenom_ctx* c) {
   cudaFree(c->dt);
   cudaFree(c->smax);
   cudaFree(c->Uhost);
+  cudaFree(c->adj);
+  cudaFree(c->adj_flags);
   for (cudaEvent_t ev : c->ev) cudaEventDestroy(ev);
   delete c;
   return TENOM_OK;
@@ -573,6 +593,140 @@ tenom_status tenom_kernel_timing(tenom_ctx* c, int enable, double* face_ms_per_l
   c->ev_used = 0;
   c->timing = enable != 0;
   return TENOM_OK;
+}
+
+/* ---------------------------------------------------------------- adjoint */
+
+size_t tenom_flags_bytes(const tenom_ctx* c) {
+  if (!c) return 0;
+  size_t b = 0;
+  for (int a = 0; a < c->g.dim; ++a) b += (size_t)c->nface[a] * c->nv * 2;
+  return b;
+}
+
+static size_t flags_offset(const tenom_ctx* c, int axis) {
+  size_t b = 0;
+  for (int a = 0; a < axis; ++a) b += (size_t)c->nface[a] * c->nv * 2;
+  return b;
+}
+
+static cudaError_t adj_sweeps(tenom_ctx* c, const double* U, const uint8_t* flags_stage, const double* w, double* Z) {
+  cudaError_t e = cudaMemsetAsync(Z, 0, sizeof(double) * c->nv * c->ncell, c->st);
+  for (int a = 0; a < c->g.dim && e == cudaSuccess; ++a) {
+    AdjArgs A;
+    memset(&A, 0, sizeof(A));
+    A.U = U;
+    A.flags = flags_stage ? flags_stage + flags_offset(c, a) : nullptr;
+    A.w = w;
+    A.Z = Z;
+    A.status = c->status;
+    for (int d = 0; d < 3; ++d) {
+      A.n[d] = c->g.n[d];
+      A.bc[d] = c->g.bc[d];
+    }
+    A.ncell = c->ncell;
+    A.dx = c->g.dx[a];
+    A.gamma = c->g.gamma;
+    A.sch = scheme_dev(c->s);
+    if (c->nv == 3) e = launch_adj_nv3(A, a, c->s.K, c->s.limiter, c->st);
+    else if (c->nv == 4) e = launch_adj_nv4(A, a, c->s.K, c->s.limiter, c->st);
+    else e = launch_adj_nv5(A, a, c->s.K, c->s.limiter, c->st);
+  }
+  return e;
+}
+
+static cudaError_t ensure_adj(tenom_ctx* c) {
+  if (c->adj) return cudaSuccess;
+  cudaError_t e = cudaMalloc(&c->adj, sizeof(double) * c->nv * c->ncell * 7);
+  if (e == cudaSuccess) e = cudaMalloc(&c->adj_flags, tenom_flags_bytes(c) * 3);
+  return e;
+}
+
+static cudaError_t lincomb(tenom_ctx* c, double* out, double c0, const double* x0, double c1, const double* x1,
+                           double c2, const double* x2, double c3, const double* dtp, const double* x3) {
+  const long long n = c->nv * c->ncell;
+  lincomb_kernel<<<ew_blocks(n), 256, 0, c->st>>>(n, out, c0, x0, c1, x1, c2, x2, c3, dtp, x3);
+  return cudaGetLastError();
+}
+
+tenom_status tenom_rhs_vjp(tenom_ctx* c, const double* U, const double* w, double* Ubar) {
+  if (!c) return TENOM_E_INVALID;
+  if (!aligned8(U) || !aligned8(w) || !aligned8(Ubar) || Ubar == U || Ubar == w)
+    return fail(c, TENOM_E_INVALID, "rhs_vjp: bad pointers");
+  cudaError_t e = adj_sweeps(c, U, nullptr, w, Ubar);
+  return e == cudaSuccess ? TENOM_OK : cuda_fail(c, e, "rhs_vjp");
+}
+
+/* one SSP-RK3 step that keeps its stage states and cutoff flags */
+static cudaError_t rk3_record(tenom_ctx* c, double* U, double* U1, double* U2, uint8_t* fl) {
+  const size_t fb = tenom_flags_bytes(c);
+  const double* src[3] = {U, U1, U2};
+  cudaError_t e = cudaSuccess;
+  for (int st = 0; st < 3 && e == cudaSuccess; ++st) {
+    for (int a = 0; a < c->g.dim && e == cudaSuccess; ++a)
+      e = launch_faces(c, src[st], a, c->face[a], fl + st * fb + flags_offset(c, a));
+    if (e != cudaSuccess) break;
+    if (st == 0) e = launch_stage(c, nullptr, U, U1, 1, 0.0, 1.0);
+    else if (st == 1) e = launch_stage(c, U, U1, U2, 2, 0.75, 0.25);
+    else e = launch_stage(c, U, U2, U, 2, 1.0 / 3.0, 2.0 / 3.0);
+  }
+  return e;
+}
+
+tenom_status tenom_rk3_step_record(tenom_ctx* c, double* U, const double* dt_dev, double* tape_states,
+                                   uint8_t* tape_flags) {
+  if (!c) return TENOM_E_INVALID;
+  if (!aligned8(U) || !aligned8(dt_dev) || !aligned8(tape_states) || !tape_flags)
+    return fail(c, TENOM_E_INVALID, "rk3_step_record: bad pointers");
+  cudaError_t e = cudaSuccess;
+  if (dt_dev != c->dt) e = cudaMemcpyAsync(c->dt, dt_dev, sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+  const long long n = c->nv * c->ncell;
+  if (e == cudaSuccess) e = rk3_record(c, U, tape_states, tape_states + n, tape_flags);
+  return e == cudaSuccess ? TENOM_OK : cuda_fail(c, e, "rk3_step_record");
+}
+
+tenom_status tenom_rk3_step_adjoint_tape(tenom_ctx* c, const double* U_n, const double* tape_states,
+                                         const uint8_t* tape_flags, const double* dt_dev, const double* Ubar_np1,
+                                         double* Ubar_n) {
+  if (!c) return TENOM_E_INVALID;
+  if (!aligned8(U_n) || !aligned8(tape_states) || !tape_flags || !aligned8(dt_dev) || !aligned8(Ubar_np1) ||
+      !aligned8(Ubar_n))
+    return fail(c, TENOM_E_INVALID, "rk3_step_adjoint: bad pointers");
+  cudaError_t e = ensure_adj(c);
+  if (e != cudaSuccess) return cuda_fail(c, e, "rk3_step_adjoint");
+  const long long n = c->nv * c->ncell;
+  const size_t fb = tenom_flags_bytes(c);
+  double *A1 = c->adj, *A2 = c->adj + n, *A3 = c->adj + 2 * n, *Z = c->adj + 3 * n;
+  const double *U1 = tape_states, *U2 = tape_states + n;
+  /* stage 3: U^{n+1} = 1/3 U^n + 2/3 (U2 + dt L(U2)) */
+  e = lincomb(c, A1, 2.0 / 3.0, Ubar_np1, 0, nullptr, 0, nullptr, 0, nullptr, nullptr);
+  if (e == cudaSuccess) e = adj_sweeps(c, U2, tape_flags + 2 * fb, A1, Z);
+  if (e == cudaSuccess) e = lincomb(c, A2, 1.0, A1, 0, nullptr, 0, nullptr, 1.0, dt_dev, Z);    /* Ubar2 */
+  /* stage 2: U2 = 3/4 U^n + 1/4 (U1 + dt L(U1)) */
+  if (e == cudaSuccess) e = lincomb(c, A3, 0.25, A2, 0, nullptr, 0, nullptr, 0, nullptr, nullptr);
+  if (e == cudaSuccess) e = adj_sweeps(c, U1, tape_flags + fb, A3, Z);
+  if (e == cudaSuccess) e = lincomb(c, A3, 1.0, A3, 0, nullptr, 0, nullptr, 1.0, dt_dev, Z);    /* Ubar1 */
+  /* stage 1: U1 = U^n + dt L(U^n) */
+  if (e == cudaSuccess) e = adj_sweeps(c, U_n, tape_flags, A3, Z);
+  if (e == cudaSuccess)
+    e = lincomb(c, Ubar_n, 1.0 / 3.0, Ubar_np1, 0.75, A2, 1.0, A3, 1.0, dt_dev, Z);
+  return e == cudaSuccess ? TENOM_OK : cuda_fail(c, e, "rk3_step_adjoint");
+}
+
+tenom_status tenom_rk3_step_adjoint(tenom_ctx* c, const double* U_n, const double* dt_dev, const double* Ubar_np1,
+                                    double* Ubar_n) {
+  if (!c) return TENOM_E_INVALID;
+  if (!aligned8(U_n) || !aligned8(dt_dev)) return fail(c, TENOM_E_INVALID, "rk3_step_adjoint: bad pointers");
+  cudaError_t e = ensure_adj(c);
+  if (e != cudaSuccess) return cuda_fail(c, e, "rk3_step_adjoint");
+  const long long n = c->nv * c->ncell;
+  double* Uc = c->adj + 4 * n;  /* copy of U^n advanced by the recording step */
+  e = cudaMemcpyAsync(Uc, U_n, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st);
+  if (e == cudaSuccess && dt_dev != c->dt)
+    e = cudaMemcpyAsync(c->dt, dt_dev, sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+  if (e == cudaSuccess) e = rk3_record(c, Uc, c->adj + 5 * n, c->adj + 6 * n, c->adj_flags);
+  if (e != cudaSuccess) return cuda_fail(c, e, "rk3_step_adjoint");
+  return tenom_rk3_step_adjoint_tape(c, U_n, c->adj + 5 * n, c->adj_flags, dt_dev, Ubar_np1, Ubar_n);
 }
 
 tenom_status tenom_check_fastmath(const double* x, double* out, long long n, void* stream) {

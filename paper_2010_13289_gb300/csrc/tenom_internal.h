@@ -39,3 +39,11 @@ SchemeDev scheme_for_device(const tenom_scheme& s);
 cudaError_t launch_rhs_divergence(int nv, double* const F[3], const int n[3], const double dx[3], long long ncell,
                                   const long long nface[3], double* out, cudaStream_t st);
 }  // namespace tenom
+
+namespace tenom {
+struct AdjArgs;
+/* Launch the adjoint face sweep of (NV, K, limiter, axis): Z += L_a'(U)^T w. */
+cudaError_t launch_adj_nv3(const AdjArgs& a, int axis, int K, int lim, cudaStream_t st);
+cudaError_t launch_adj_nv4(const AdjArgs& a, int axis, int K, int lim, cudaStream_t st);
+cudaError_t launch_adj_nv5(const AdjArgs& a, int axis, int K, int lim, cudaStream_t st);
+}  // namespace tenom

@@ -66,6 +66,15 @@ def lib():
         L.tenom_last_error.restype = ctypes.c_char_p
         L.tenom_kernel_timing.argtypes = [VP, c_int, P(c_double), P(ctypes.c_longlong)]
         L.tenom_fp64_peak.argtypes = [VP, c_int, c_int, P(c_double)]
+        L.tenom_flags_bytes.argtypes = [VP]
+        L.tenom_flags_bytes.restype = ctypes.c_size_t
+        L.tenom_rhs_vjp.argtypes = [VP, VP, VP, VP]
+        L.tenom_rk3_step_record.argtypes = [VP, VP, VP, VP, VP]
+        L.tenom_rk3_step_adjoint_tape.argtypes = [VP, VP, VP, VP, VP, VP, VP]
+        L.tenom_rk3_step_adjoint.argtypes = [VP, VP, VP, VP, VP]
+        for name in ("tenom_rhs_vjp", "tenom_rk3_step_record", "tenom_rk3_step_adjoint_tape",
+                     "tenom_rk3_step_adjoint"):
+            getattr(L, name).restype = c_int
         L.tenom_check_fastmath.argtypes = [VP, VP, ctypes.c_longlong, VP]
         L.tenom_check_fastmath.restype = c_int
         L.tenom_rhs_noalloc.argtypes = [P(tenom_grid), P(tenom_scheme), VP, VP, VP, VP]
@@ -242,6 +251,38 @@ class Solver:
         self._check(lib().tenom_face_dump(self._ctx, _ptr(U), axis, _ptr(F), _ptr(fl) if fl is not None else None),
                     "tenom_face_dump")
         return F, fl
+
+    # ---- frozen-branch adjoint ----
+    def flags_bytes(self):
+        return int(lib().tenom_flags_bytes(self._ctx))
+
+    def rhs_vjp(self, U, w, out=None):
+        """L'(U)^T w."""
+        out = self.tensor() if out is None else out
+        self._check(lib().tenom_rhs_vjp(self._ctx, _ptr(U), _ptr(w), _ptr(out)), "tenom_rhs_vjp")
+        return out
+
+    def new_tape(self):
+        import torch
+        states = torch.empty((2,) + self.state_shape, dtype=torch.float64, device="cuda")
+        flags = torch.empty(3 * self.flags_bytes(), dtype=torch.uint8, device="cuda")
+        return states, flags
+
+    def rk3_step_record(self, U, dt_dev, tape):
+        states, flags = tape
+        self._check(lib().tenom_rk3_step_record(self._ctx, _ptr(U), _ptr(dt_dev), _ptr(states), _ptr(flags)),
+                    "tenom_rk3_step_record")
+        return U
+
+    def rk3_step_adjoint(self, U_n, dt_dev, Ubar_np1, tape=None, out=None):
+        out = self.tensor() if out is None else out
+        if tape is None:
+            st = lib().tenom_rk3_step_adjoint(self._ctx, _ptr(U_n), _ptr(dt_dev), _ptr(Ubar_np1), _ptr(out))
+        else:
+            st = lib().tenom_rk3_step_adjoint_tape(self._ctx, _ptr(U_n), _ptr(tape[0]), _ptr(tape[1]),
+                                                   _ptr(dt_dev), _ptr(Ubar_np1), _ptr(out))
+        self._check(st, "tenom_rk3_step_adjoint")
+        return out
 
     def status(self, reset=False):
         v = ctypes.c_int(0)
