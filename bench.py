@@ -33,6 +33,10 @@ BATCH_WORKLOADS = {
     # name: (problems, seed, nmin, nmax, K, limiter)
     "batched_riemann_512_teno6_mp": (512, 4, 128, 8192, 6, 0),
 }
+ADJOINT_WORKLOADS = {
+    # name: (n, seed, steps, window, checkpoint_every, K, limiter)
+    "adjoint_broadband_2d_512_teno6_mp": (512, 5, 200, 64, 20, 6, 0),
+}
 DEFAULT = "broadband_2d_2048_teno6_mp"
 FP64_NOMINAL = 1.25e12  # FLOP/s, GB300 FP64 (an FMA counts 2)
 
@@ -476,13 +480,103 @@ def run_batch(args):
         torch.distributed.destroy_process_group()
 
 
+def run_adjoint(args):
+    """Adjoint workload: 2D 512^2 broadband field with circular jumps, TENO6-MP, 200 SSP-RK3
+    steps at a fixed dt, loss = integral of p over a seeded 64 x 64 window at the end;
+    gradient with respect to the initial density through the frozen-branch adjoint with
+    checkpoints every 20 steps (torch.autograd); central differences on 16 seeded unit
+    directions.  Reports the backward pass's cell-updates/s per RK stage and the
+    adjoint/forward cost ratio per step."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2010_13289_gb300 import problems as PB
+    from paper_2010_13289_gb300 import tenom as T
+    from paper_2010_13289_gb300.autograd import rollout
+    name = args.workload
+    n, seed, steps, win_n, every, K, lim = ADJOINT_WORKLOADS[name]
+    prim, dx = PB.broadband_2d(n, seed)
+    rng = np.random.default_rng(seed)
+    wy, wx = rng.integers(0, n - win_n, 2)
+    win = (slice(int(wy), int(wy) + win_n), slice(int(wx), int(wx) + win_n))
+    S = T.Solver((n, n), (dx, dx), (T.BC_PERIODIC,) * 2, T.make_scheme(K, limiter=lim))
+    primd = torch.from_numpy(prim).cuda()
+    dt = S.max_dt(S.init_state(primd), 0.4).item()
+    gam = 1.4
+    stream = torch.cuda.current_stream()
+
+    def loss_of(rho0, grad=False):
+        pr = primd.clone()
+        pr[0] = rho0
+        U0 = S.init_state(pr)
+        if grad:
+            U0.requires_grad_(True)
+        UN = rollout(U0, S, dt, steps, checkpoint_every=every)
+        rho, mx, my, E = UN[0], UN[1], UN[2], UN[3]
+        p = (gam - 1.0) * (E - 0.5 * (mx * mx + my * my) / rho)
+        return (p[win] * dx * dx).sum(), U0
+
+    # warm-up
+    L, U0 = loss_of(primd[0], grad=True)
+    L.backward()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    e0.record(stream)
+    L, U0 = loss_of(primd[0], grad=True)
+    e1.record(stream)
+    L.backward()
+    e2.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    fwd_ms = e0.elapsed_time(e1)
+    bwd_ms = e1.elapsed_time(e2)
+    Ub = U0.grad
+    u, v = primd[1], primd[2]
+    grad_rho = Ub[0] + u * Ub[1] + v * Ub[2] + 0.5 * (u * u + v * v) * Ub[3]
+    gnorm = float(torch.linalg.norm(grad_rho))
+    # central differences on 16 seeded unit directions (step 1e-8)
+    rng = np.random.default_rng(seed + 16)
+    fd_err = []
+    with torch.no_grad():
+        for _ in range(16):
+            d = torch.from_numpy(rng.normal(size=(n, n))).cuda()
+            d /= torch.linalg.norm(d)
+            Lp, _ = loss_of(primd[0] + 1e-8 * d)
+            Lm, _ = loss_of(primd[0] - 1e-8 * d)
+            fd = (Lp - Lm).item() / 2e-8
+            ad = float((grad_rho * d).sum())
+            fd_err.append(abs(fd - ad) / gnorm)
+    ncell = n * n
+    value = float(ncell) * 3 * steps / (bwd_ms * 1e-3)
+    out = {"metric": "cell-updates/s per RK stage (FP64)", "value": value, "unit": "cell-updates/s",
+           "n_gpus": 1, "steps": steps, "warmup": 1, "ms_per_step": bwd_ms / steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded, shaped like the paper's workloads)",
+           "config": {"workload": name, "shape": [n, n], "K": K, "limiter": "MP" if lim == 0 else "TVD5",
+                      "window": win_n, "checkpoint_every": every, "dt": dt,
+                      "pass": "backward (frozen-branch adjoint, segment recomputation included)"},
+           "adjoint_forward_ratio": bwd_ms / fwd_ms,
+           "forward_ms_per_step": fwd_ms / steps, "backward_ms_per_step": bwd_ms / steps,
+           "loss": L.item(), "grad_norm": gnorm,
+           "fd_check": {"directions": 16, "step": 1e-8, "max_err_over_grad_norm": max(fd_err),
+                        "median_err_over_grad_norm": float(np.median(fd_err))},
+           "clocks": clk}
+    print(json.dumps(out), flush=True)
+    S.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=DEFAULT, choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT,
+                    choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(ADJOINT_WORKLOADS))
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--ref-seconds", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -493,6 +587,8 @@ def main():
         run_reference(args)
     elif args.workload in BATCH_WORKLOADS:
         run_batch(args)
+    elif args.workload in ADJOINT_WORKLOADS:
+        run_adjoint(args)
     else:
         run_ours(args)
 
