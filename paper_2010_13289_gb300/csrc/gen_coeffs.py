@@ -177,6 +177,14 @@ def main():
         out.append("  return %s;" % acc)
         out.append("}")
     out.append("")
+    out.append("/* K-point central reconstruction sum_k d_k f_k (all candidates smooth), c = index of f_i */")
+    for K in (6, 8):
+        j0, r = FULL[K]
+        cs = face_coeffs(j0, r)
+        terms = " + ".join("(%s) * v[c + %d]" % (lit(cs[m]), j0 + m) for m in range(r))
+        out.append("template <int c> __device__ __forceinline__ double central%d(const double* v) { return %s; }"
+                   % (K, terms))
+    out.append("")
     for K in (6, 8):
         d = optimal_weights(K)
         out.append("/* maximal-order optimal weights d_k, K = %d */" % K)

@@ -74,6 +74,10 @@ template <int e> __device__ __forceinline__ double betaK8(const double* D) {
   return (2.234854870582735) * (t0 * t0) + (3.6638884397833413) * (t1 * t1) + (5.644238245592201) * (t2 * t2) + (7.367729894004351) * (t3 * t3) + (2.9756305436346877) * (t4 * t4) + (0.26204645894217) * (t5 * t5) + (0.00612798797104159) * (t6 * t6);
 }
 
+/* K-point central reconstruction sum_k d_k f_k (all candidates smooth), c = index of f_i */
+template <int c> __device__ __forceinline__ double central6(const double* v) { return (0.016666666666666666) * v[c + -2] + (-0.13333333333333333) * v[c + -1] + (0.6166666666666667) * v[c + 0] + (0.6166666666666667) * v[c + 1] + (-0.13333333333333333) * v[c + 2] + (0.016666666666666666) * v[c + 3]; }
+template <int c> __device__ __forceinline__ double central8(const double* v) { return (-0.0035714285714285713) * v[c + -3] + (0.034523809523809526) * v[c + -2] + (-0.16547619047619047) * v[c + -1] + (0.6345238095238095) * v[c + 0] + (0.6345238095238095) * v[c + 1] + (-0.16547619047619047) * v[c + 2] + (0.034523809523809526) * v[c + 3] + (-0.0035714285714285713) * v[c + 4]; }
+
 /* maximal-order optimal weights d_k, K = 6 */
 __device__ __forceinline__ double dopt6(int k) {
   switch (k) {

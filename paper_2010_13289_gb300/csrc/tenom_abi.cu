@@ -165,11 +165,12 @@ __global__ void advance_time_kernel(double* t, const double* dt) { *t = *t + *dt
 __global__ void fastmath_check_kernel(const double* x, double* out, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double v = x[i];
-    out[4 * i + 0] = rcp_nr(v);
-    out[4 * i + 1] = 1.0 / v;
+    out[5 * i + 0] = rcp_nr(v);
+    out[5 * i + 1] = 1.0 / v;
     const double r = rsqrt_nr(v);
-    out[4 * i + 2] = v * r;
-    out[4 * i + 3] = sqrt(v);
+    out[5 * i + 2] = v * r;
+    out[5 * i + 3] = sqrt(v);
+    out[5 * i + 4] = rcp_nr1(v);
   }
 }
 
@@ -240,6 +241,9 @@ static tenom_status cuda_fail(tenom_ctx* c, cudaError_t e, const char* where) {
   return fail(c, TENOM_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
+static const double kDopt6[4] = {9.0 / 20.0, 3.0 / 10.0, 1.0 / 20.0, 1.0 / 5.0};
+static const double kDopt8[6] = {3.0 / 7.0, 9.0 / 35.0, 2.0 / 35.0, 6.0 / 35.0, 1.0 / 70.0, 1.0 / 14.0};
+
 static SchemeDev scheme_dev(const tenom_scheme& s) {
   SchemeDev d;
   memset(&d, 0, sizeof(d));
@@ -250,11 +254,12 @@ static SchemeDev scheme_dev(const tenom_scheme& s) {
   d.mp_alpha = s.mp_alpha;
   d.mp_beta_third = s.mp_beta / 3.0;
   for (int k = 0; k < 6; ++k) d.d[k] = s.d[k];
+  d.default_d = 1;
+  for (int k = 0; k < s.K - 2; ++k)
+    if (s.d[k] != ((s.K == 6) ? kDopt6[k] : kDopt8[k])) d.default_d = 0;
   return d;
 }
 
-static const double kDopt6[4] = {9.0 / 20.0, 3.0 / 10.0, 1.0 / 20.0, 1.0 / 5.0};
-static const double kDopt8[6] = {3.0 / 7.0, 9.0 / 35.0, 2.0 / 35.0, 6.0 / 35.0, 1.0 / 70.0, 1.0 / 14.0};
 
 extern "C" {
 

@@ -57,6 +57,13 @@ __device__ __forceinline__ double rcp_nr(double x) {
   return fma(y, e, y);
 }
 
+/* 1/x by one Newton-Raphson step: for quantities that only feed a comparison
+   (the cutoff's gamma_k, TENO8A's eta); accuracy checked by the GPU tests */
+__device__ __forceinline__ double rcp_nr1(double x) {
+  const double y = rcp_approx(x);
+  return fma(y, fma(-x, y, 1.0), y);
+}
+
 /* 1/sqrt(x) by two Newton steps for positive normal x; sqrt(x) = x * rsqrt(x) */
 __device__ __forceinline__ double rsqrt_nr(double x) {
   double y = rsqrt_approx(x);

@@ -34,7 +34,7 @@ struct SchemeDev {
   int ct_mode;
   int mp_curv;
   int weights;
-  int pad_;
+  int default_d;         /* d_k are the maximal-order weights (central formula applies) */
   double ct_const;
   double mp_alpha;
   double mp_beta_third;  /* mp_beta / 3 */
@@ -116,7 +116,7 @@ __device__ __forceinline__ double adaptive_ct(const double* D, int* e) {
   for (int q = 0; q < 4; ++q) {
     /* eta_{i-1+q}: Delta f_{j+1/2} = D[c + j], Delta f_{j-1/2} = D[c + j - 1] with j = q - 1 */
     const double dfp = D[c + q - 1], dfm = D[c + q - 2];
-    const double eta = (iabs(2.0 * dfp * dfm) + eps) * rcp_nr(dfp * dfp + dfm * dfm + eps);
+    const double eta = (iabs(2.0 * dfp * dfm) + eps) * rcp_nr1(dfp * dfp + dfm * dfm + eps);
     eh = (q == 0) ? eta : imin(eh, eta);
   }
   const double m = 1.0 - imin(1.0, eh * (1.0 / Cr));
@@ -139,18 +139,12 @@ __device__ __forceinline__ double teno_m(const double (&v)[K], const SchemeDev& 
 #pragma unroll
   for (int t = 0; t < K - 1; ++t) D[t] = v[t + 1] - v[t];
   double fk[nk], bk[nk];
-  fk[0] = cand0<c>(v);
-  fk[1] = cand1<c>(v);
-  fk[2] = cand2<c>(v);
-  fk[3] = cand3<c>(v);
   bk[0] = beta0<c - 1>(D);
   bk[1] = beta1<c>(D);
   bk[2] = beta2<c - 2>(D);
   bk[3] = beta3<c>(D);
   double bK;
   if constexpr (K == 8) {
-    fk[4] = cand4<c>(v);
-    fk[5] = cand5<c>(v);
     bk[4] = beta4<c - 3>(D);
     bk[5] = beta5<c>(D);
     bK = betaK8<0>(D);
@@ -161,7 +155,7 @@ __device__ __forceinline__ double teno_m(const double (&v)[K], const SchemeDev& 
   double gk[nk], sum = 0.0;
 #pragma unroll
   for (int k = 0; k < nk; ++k) {
-    const double x = fma(tau, rcp_nr(bk[k] + 1e-40), 1.0);
+    const double x = fma(tau, rcp_nr1(bk[k] + 1e-40), 1.0);
     const double x3 = x * x * x;
     gk[k] = x3 * x3;
     sum += gk[k];
@@ -176,6 +170,20 @@ __device__ __forceinline__ double teno_m(const double (&v)[K], const SchemeDev& 
   for (int k = 0; k < nk; ++k) bits |= (ilt_nonneg(gk[k], thr) ? 0u : 1u) << k;
   if (dbits(sum) >= 0x7ff0000000000000ll) st |= ST_NONFINITE;
   flag = bits | ((unsigned)((ex - 7) & 3) << 6);
+  constexpr unsigned all = (1u << nk) - 1u;
+  if (bits == all && S.default_d) {
+    /* every candidate smooth: sum_k d_k f_k is the K-point central scheme */
+    if constexpr (K == 8) return central8<c>(v);
+    else return central6<c>(v);
+  }
+  fk[0] = cand0<c>(v);
+  fk[1] = cand1<c>(v);
+  fk[2] = cand2<c>(v);
+  fk[3] = cand3<c>(v);
+  if constexpr (K == 8) {
+    fk[4] = cand4<c>(v);
+    fk[5] = cand5<c>(v);
+  }
   if (S.weights == W_TENO) {
     double num = 0.0, den = 0.0;
 #pragma unroll
@@ -183,7 +191,7 @@ __device__ __forceinline__ double teno_m(const double (&v)[K], const SchemeDev& 
       if (bits >> k & 1u) { num += S.d[k] * fk[k]; den += S.d[k]; }
     return num / den;
   }
-  if (bits != (1u << nk) - 1u) {
+  if (bits != all) {
     if constexpr (LIM == LIM_MP) {
       double fmin, fmax;
       mp_bounds<c>(v, S, fmin, fmax);

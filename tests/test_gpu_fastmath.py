@@ -19,16 +19,19 @@ def test_newton_reciprocal_and_sqrt_within_two_ulp():
     x = np.concatenate([10.0 ** rng.uniform(-300, 300, 200000), 1e-40 + 10.0 ** rng.uniform(-60, -30, 20000),
                         rng.uniform(0.5, 2.0, 20000), [1.0, 2.0, 0.1, 1e-40, 3.0]])
     xd = torch.from_numpy(x).cuda()
-    out = torch.empty(4 * x.size, dtype=torch.float64, device="cuda")
+    out = torch.empty(5 * x.size, dtype=torch.float64, device="cuda")
     st = T.lib().tenom_check_fastmath(ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(out.data_ptr()), x.size,
                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == T.TENOM_OK
-    o = out.cpu().numpy().reshape(-1, 4)
+    o = out.cpu().numpy().reshape(-1, 5)
     ulp_r = np.abs(o[:, 0] - o[:, 1]) / np.spacing(np.abs(o[:, 1]))
     ulp_s = np.abs(o[:, 2] - o[:, 3]) / np.spacing(np.abs(o[:, 3]))
     assert np.all(np.isfinite(o))
     assert ulp_r.max() <= 2.0, ulp_r.max()
     assert ulp_s.max() <= 2.0, ulp_s.max()
+    # one Newton step (used only where a comparison follows): relative error <= 1e-12
+    rel1 = np.abs(o[:, 4] - o[:, 1]) / np.abs(o[:, 1])
+    assert rel1.max() <= 1e-12, rel1.max()
     # CUDA's 1/x and sqrt are correctly rounded: the host agrees with them exactly
     np.testing.assert_array_equal(o[:, 1], 1.0 / x)
     np.testing.assert_array_equal(o[:, 3], np.sqrt(x))
