@@ -79,7 +79,13 @@ typedef struct tenom_scheme {
   int mp_curv;      /* TENOM_CURV_* */
   int weights;      /* TENOM_W_* */
   double d[6];      /* optimal weights d_0..d_{K-3}; all zero = maximal-order default */
+  int decisions;    /* TENOM_DECIDE_FILTERED (default): cutoff decisions certified in FP32 and
+                       decided in FP64 where the FP32 bounds do not settle them (same outcome
+                       as FP64); TENOM_DECIDE_FP64: FP64 only */
+  int reserved;
 } tenom_scheme;
+
+enum { TENOM_DECIDE_FILTERED = 0, TENOM_DECIDE_FP64 = 1 };
 
 typedef struct tenom_ctx tenom_ctx;
 

@@ -160,7 +160,9 @@ def main():
                    % (k, terms))
     out.append("")
     out.append("/* Smoothness indicators as sums of squares of difference combinations;")
-    out.append("   D[t] = v[t+1] - v[t], e = index in D of the stencil's first difference. */")
+    out.append("   D[t] = v[t+1] - v[t], e = index in D of the stencil's first difference.  With ABS the")
+    out.append("   coefficients are replaced by their magnitudes (evaluated on |D| this bounds the")
+    out.append("   rounding error of the form).  T: double, or float for the certified cutoff filter. */")
     names = [("beta%d" % k, j0, r) for k, (j0, r) in enumerate(CAND)] + \
             [("betaK%d" % K, FULL[K][0], FULL[K][1]) for K in (6, 8)]
     for name, j0, r in names:
@@ -168,11 +170,16 @@ def main():
         n = r - 1
         body = []
         for t in range(n):
-            terms = ["D[e + %d]" % t] + ["(%s) * D[e + %d]" % (lit(L[u][t]), u) for u in range(t + 1, n)]
-            body.append("  const double t%d = %s;" % (t, " + ".join(terms)))
-        acc = " + ".join("(%s) * (t%d * t%d)" % (lit(w[t]), t, t) for t in range(n))
-        out.append("/* %s: cells i%+d..i%+d */" % (name, j0, j0 + r - 1))
-        out.append("template <int e> __device__ __forceinline__ double %s(const double* D) {" % name)
+            terms = ["D[e + %d]" % t]
+            for u in range(t + 1, n):
+                if L[u][t] != 0:
+                    terms.append("T(ABS ? %s : %s) * D[e + %d]" % (lit(abs(L[u][t])), lit(L[u][t]), u))
+            body.append("  const T t%d = %s;" % (t, " + ".join(terms)))
+        acc = " + ".join("T(%s) * (t%d * t%d)" % (lit(w[t]), t, t) for t in range(n))
+        out.append("/* %s: cells i%+d..i%+d (ABS: the same form with |coefficients|, for error bounds) */"
+                   % (name, j0, j0 + r - 1))
+        out.append("template <int e, bool ABS = false, class T = double>")
+        out.append("__device__ __forceinline__ T %s(const T* D) {" % name)
         out.extend(body)
         out.append("  return %s;" % acc)
         out.append("}")

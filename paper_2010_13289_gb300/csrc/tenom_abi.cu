@@ -254,6 +254,7 @@ static SchemeDev scheme_dev(const tenom_scheme& s) {
   d.mp_alpha = s.mp_alpha;
   d.mp_beta_third = s.mp_beta / 3.0;
   for (int k = 0; k < 6; ++k) d.d[k] = s.d[k];
+  d.exact_decisions = (s.decisions == TENOM_DECIDE_FP64) ? 1 : 0;
   d.default_d = 1;
   for (int k = 0; k < s.K - 2; ++k)
     if (s.d[k] != ((s.K == 6) ? kDopt6[k] : kDopt8[k])) d.default_d = 0;
@@ -303,6 +304,10 @@ static tenom_status validate(const tenom_grid* g, const tenom_scheme* s, std::st
   if (s->ct_mode != TENOM_CT_CONST && s->ct_mode != TENOM_CT_ADAPTIVE) { *msg = "bad ct_mode"; return TENOM_E_INVALID; }
   if (s->mp_curv != TENOM_CURV_M4 && s->mp_curv != TENOM_CURV_MM) { *msg = "bad mp_curv"; return TENOM_E_INVALID; }
   if (s->weights != TENOM_W_TENOM && s->weights != TENOM_W_TENO) { *msg = "bad weights"; return TENOM_E_INVALID; }
+  if (s->decisions != TENOM_DECIDE_FILTERED && s->decisions != TENOM_DECIDE_FP64) {
+    *msg = "bad decisions mode";
+    return TENOM_E_INVALID;
+  }
   for (int a = 0; a < g->dim; ++a)
     if (g->n[a] < s->K / 2 && g->bc[a] == TENOM_BC_PERIODIC) {
       *msg = "periodic axis shorter than the half stencil";

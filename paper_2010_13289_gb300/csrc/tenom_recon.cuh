@@ -35,6 +35,8 @@ struct SchemeDev {
   int mp_curv;
   int weights;
   int default_d;         /* d_k are the maximal-order weights (central formula applies) */
+  int exact_decisions;   /* 1: decide the cutoff in FP64 only (no certified FP32 filter) */
+  int pad_;
   double ct_const;
   double mp_alpha;
   double mp_beta_third;  /* mp_beta / 3 */
@@ -129,6 +131,122 @@ __device__ __forceinline__ double adaptive_ct(const double* D, int* e) {
   return ex == 7 ? 1e-7 : (ex == 8 ? 1e-8 : (ex == 9 ? 1e-9 : 1e-10));
 }
 
+/* Certified single-precision evaluation of the cutoff decisions delta_k (and of [beta] of
+   TENO8A).  FP32 runs on the SM's wide FP32 pipe; GB300's FP64 pipe is the bottleneck.
+   Every FP32 indicator is evaluated together with its absolute-value form (same form,
+   |coefficients|, on |D|), which bounds its rounding error: for a form with n differences,
+   |beta_fp32 - beta| <= (3n + 7) u beta_abs with u = 2^-24 (dot-product error analysis,
+   including the conversion of D to FP32); C = 64 u doubles that.  The bounds are carried
+   through tau, gamma_k = (1 + tau/beta_k)^6 (scaled by the largest gamma to stay in range)
+   and the comparison gamma_k < C_T sum gamma.  A decision is returned only when the whole
+   interval lies on one side; otherwise (and for out-of-range data or an indicator that may
+   vanish, where epsilon = 1e-40 matters) the caller decides in FP64.  Certified decisions
+   equal the exact-arithmetic decisions, hence those of the FP64 path except where that
+   path is itself within its rounding of the threshold (an adaptive-precision predicate in
+   the sense of Shewchuk's robust geometric predicates). */
+template <int K>
+__device__ __forceinline__ bool cutoff_filter(const double (&D)[K - 1], const SchemeDev& S, unsigned& bits, int& ex) {
+  constexpr int c = K / 2 - 1;
+  constexpr int nk = K - 2;
+  const float u = 5.9604645e-8f;
+  const float C = 64.f * u;
+  float d[K - 1], a[K - 1];
+  float dmax = 0.f;
+#pragma unroll
+  for (int t = 0; t < K - 1; ++t) {
+    d[t] = __double2float_rn(D[t]);
+    a[t] = fabsf(d[t]);
+    dmax = fmaxf(dmax, a[t]);
+  }
+  if (!(dmax <= 1e15f) || (dmax > 0.f && dmax < 1e-15f)) return false;
+  float b[nk], e[nk];
+  b[0] = beta0<c - 1, false, float>(d);
+  e[0] = beta0<c - 1, true, float>(a);
+  b[1] = beta1<c, false, float>(d);
+  e[1] = beta1<c, true, float>(a);
+  b[2] = beta2<c - 2, false, float>(d);
+  e[2] = beta2<c - 2, true, float>(a);
+  b[3] = beta3<c, false, float>(d);
+  e[3] = beta3<c, true, float>(a);
+  float bK, eK;
+  if constexpr (K == 8) {
+    b[4] = beta4<c - 3, false, float>(d);
+    e[4] = beta4<c - 3, true, float>(a);
+    b[5] = beta5<c, false, float>(d);
+    e[5] = beta5<c, true, float>(a);
+    bK = betaK8<0, false, float>(d);
+    eK = betaK8<0, true, float>(a);
+  } else {
+    bK = betaK6<0, false, float>(d);
+    eK = betaK6<0, true, float>(a);
+  }
+  const float comb = (b[1] + b[2] + 4.f * b[0]) * (1.f / 6.f);
+  const float tau = fabsf(bK - comb);
+  const float dtau = C * (eK + (e[1] + e[2] + 4.f * e[0]) * (1.f / 6.f)) + 8.f * u * (bK + comb);
+  const float tl = fmaxf(tau - dtau, 0.f), th = tau + dtau;
+  float xl[nk], xh[nk], xm = 1.f;
+#pragma unroll
+  for (int k = 0; k < nk; ++k) {
+    const float bl = b[k] - C * e[k], bh = (b[k] + C * e[k]) * (1.f + 2.f * u);
+    if (bl < 1e-30f) {
+      if (th != 0.f) return false;  /* beta_k may vanish: epsilon matters */
+      xl[k] = 1.f;
+      xh[k] = 1.f;
+    } else {
+      xl[k] = (1.f + (tl / bh) * (1.f - 3.f * u)) * (1.f - u);
+      xh[k] = (1.f + (th / bl) * (1.f + 3.f * u)) * (1.f + u);
+      if (!(xh[k] < 1e30f)) return false;
+    }
+    xm = fmaxf(xm, xh[k]);
+  }
+  const float rxm = 1.f / xm;
+  float gl[nk], gh[nk], Sl = 0.f, Sh = 0.f;
+#pragma unroll
+  for (int k = 0; k < nk; ++k) {
+    const float yl = xl[k] * rxm * (1.f - 3.f * u), yh = xh[k] * rxm * (1.f + 3.f * u);
+    const float yl3 = yl * yl * yl, yh3 = yh * yh * yh;
+    gl[k] = yl3 * yl3 * (1.f - 8.f * u);
+    gh[k] = yh3 * yh3 * (1.f + 8.f * u);
+    Sl += gl[k];
+    Sh += gh[k];
+  }
+  Sl *= 1.f - 8.f * u;
+  Sh *= 1.f + 8.f * u;
+  double CT = S.ct_const;
+  ex = 7;
+  if (S.ct_mode == CT_ADAPTIVE) {
+    const float xi = 1e-3f, Cr = 0.23f, a1 = 10.5f, a2 = 3.5f;
+    const float eps = 0.9f * Cr / (1.f - 0.9f * Cr) * xi * xi;
+    float eh = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float dfp = d[c + q - 1], dfm = d[c + q - 2];
+      const float eta = (fabsf(2.f * dfp * dfm) + eps) / (dfp * dfp + dfm * dfm + eps);
+      eh = (q == 0) ? eta : fminf(eh, eta);
+    }
+    const float m = 1.f - fminf(1.f, eh / Cr);
+    const float om = 1.f - m;
+    const float g = om * om * om * om * (1.f + 4.f * m);
+    const float beta = a1 - a2 * (1.f - g);
+    if (fabsf(beta - rintf(beta)) < 1e-3f) return false;
+    int x = (int)floorf(beta);
+    x = x < 7 ? 7 : (x > 10 ? 10 : x);
+    ex = x;
+    CT = x == 7 ? 1e-7 : (x == 8 ? 1e-8 : (x == 9 ? 1e-9 : 1e-10));
+  }
+  const float CTf = __double2float_rn(CT);
+  const float thl = CTf * (1.f - 2.f * u) * Sl * (1.f - u), thh = CTf * (1.f + 2.f * u) * Sh * (1.f + u);
+  unsigned bt = 0;
+#pragma unroll
+  for (int k = 0; k < nk; ++k) {
+    if (gh[k] < thl) continue;            /* certainly chi_k < C_T: delta_k = 0 */
+    if (gl[k] >= thh) bt |= 1u << k;      /* certainly chi_k >= C_T: delta_k = 1 */
+    else return false;
+  }
+  bits = bt;
+  return true;
+}
+
 /* One TENO-M reconstruction.  flag receives delta bits | ([beta]-7) << 6; st receives
    ST_NONFINITE when an indicator is not finite. */
 template <int K, int LIM>
@@ -138,7 +256,11 @@ __device__ __forceinline__ double teno_m(const double (&v)[K], const SchemeDev& 
   double D[K - 1];
 #pragma unroll
   for (int t = 0; t < K - 1; ++t) D[t] = v[t + 1] - v[t];
-  double fk[nk], bk[nk];
+  double fk[nk];
+  unsigned bits = 0;
+  int ex = 7;
+  if (S.exact_decisions || !cutoff_filter<K>(D, S, bits, ex)) {
+  double bk[nk];
   bk[0] = beta0<c - 1>(D);
   bk[1] = beta1<c>(D);
   bk[2] = beta2<c - 2>(D);
@@ -161,14 +283,14 @@ __device__ __forceinline__ double teno_m(const double (&v)[K], const SchemeDev& 
     sum += gk[k];
   }
   double CT = S.ct_const;
-  int ex = 7;
   if (S.ct_mode == CT_ADAPTIVE) CT = adaptive_ct<c>(D, &ex);
   /* chi_k < C_T  <=>  gamma_k < C_T sum gamma (all positive: compared as bit patterns) */
   const double thr = CT * sum;
-  unsigned bits = 0;
+  bits = 0;
 #pragma unroll
   for (int k = 0; k < nk; ++k) bits |= (ilt_nonneg(gk[k], thr) ? 0u : 1u) << k;
   if (dbits(sum) >= 0x7ff0000000000000ll) st |= ST_NONFINITE;
+  }
   flag = bits | ((unsigned)((ex - 7) & 3) << 6);
   constexpr unsigned all = (1u << nk) - 1u;
   if (bits == all && S.default_d) {

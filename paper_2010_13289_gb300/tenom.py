@@ -30,7 +30,11 @@ class tenom_grid(ctypes.Structure):
 class tenom_scheme(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int), ("limiter", ctypes.c_int), ("ct_mode", ctypes.c_int),
                 ("ct_const", ctypes.c_double), ("mp_alpha", ctypes.c_double), ("mp_beta", ctypes.c_double),
-                ("mp_curv", ctypes.c_int), ("weights", ctypes.c_int), ("d", ctypes.c_double * 6)]
+                ("mp_curv", ctypes.c_int), ("weights", ctypes.c_int), ("d", ctypes.c_double * 6),
+                ("decisions", ctypes.c_int), ("reserved", ctypes.c_int)]
+
+
+DECIDE_FILTERED, DECIDE_FP64 = 0, 1
 
 
 class TenomError(RuntimeError):
@@ -117,7 +121,7 @@ def make_grid(shape, dx, bc, gamma=1.4):
 
 
 def make_scheme(K=6, limiter=LIM_MP, ct_mode=None, ct_const=1e-5, mp_alpha=1.25, mp_beta=4.0, mp_curv=CURV_M4,
-                weights=W_TENOM, d=None):
+                weights=W_TENOM, d=None, decisions=DECIDE_FILTERED):
     s = tenom_scheme()
     st = lib().tenom_scheme_default(ctypes.byref(s), K)
     if st != TENOM_OK:
@@ -130,6 +134,7 @@ def make_scheme(K=6, limiter=LIM_MP, ct_mode=None, ct_const=1e-5, mp_alpha=1.25,
     s.mp_beta = mp_beta
     s.mp_curv = mp_curv
     s.weights = weights
+    s.decisions = decisions
     if d is not None:
         for k in range(6):
             s.d[k] = d[k] if k < len(d) else 0.0

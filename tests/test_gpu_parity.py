@@ -225,3 +225,36 @@ def test_full_size_3d_sampled(T, orc):
     S, g, so, Uo, Ug = setup(T, orc, (256, 256, 256), (0, 0, 0), 8, 0, prim, dx=(dx, dx, dx))
     del prim
     check_sampled(T, orc, S, g, so, Ug, Uo, (256, 256, 256), 3000, 3)
+
+
+FILTER_CASES = [
+    ("random", (300,), (1,), 6, 0), ("random", (300,), (0,), 8, 1), ("random", (70, 45), (1, 0), 8, 0),
+    ("random", (20, 13, 11), (0, 1, 0), 6, 1), ("random", (33, 40), (0, 0), 8, 1),
+    ("broadband", (2048, 2048), (0, 0), 6, 0), ("broadband", (2048, 2048), (0, 0), 8, 1),
+    ("solenoidal", (96, 96, 96), (0, 0, 0), 8, 0),
+]
+
+
+@pytest.mark.parametrize("kind,shape,bc,K,lim", FILTER_CASES)
+def test_certified_fp32_cutoff_filter_equals_fp64_decisions(T, kind, shape, bc, K, lim):
+    """The cutoff decisions taken through the certified FP32 filter (default) are identical to
+    FP64-only decisions, and so are the face fluxes, bit for bit."""
+    if kind == "random":
+        prim = PB.random_state(tuple(reversed(shape)), seed=sum(shape) + 3 * K + lim, jumps=True)
+        dx = tuple(1.0 / n for n in shape)
+    elif kind == "broadband":
+        prim, h = PB.broadband_2d(shape[0], 2)
+        dx = (h, h)
+    else:
+        prim, h = PB.solenoidal_3d(shape[0], 3)
+        dx = (h, h, h)
+    S1 = T.Solver(shape, dx, bc, T.make_scheme(K, limiter=lim))
+    S2 = T.Solver(shape, dx, bc, T.make_scheme(K, limiter=lim, decisions=T.DECIDE_FP64))
+    U = S1.init_state(torch.from_numpy(prim).cuda())
+    for a in range(len(shape)):
+        F1, f1 = S1.face_dump(U, a)
+        F2, f2 = S2.face_dump(U, a)
+        assert torch.equal(f1, f2), int((f1 != f2).sum())
+        assert torch.equal(F1, F2)
+    S1.close()
+    S2.close()
