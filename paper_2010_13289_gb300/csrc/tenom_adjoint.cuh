@@ -164,14 +164,33 @@ __device__ __forceinline__ void cand_coeffs(int k, double* g) {
 }
 
 /* omega with fhat = sum_q omega_q v_q under the frozen flags (delta bits in `bits`) */
+template <int K>
+__device__ __forceinline__ void central_weights(double (&om)[K]) {
+  constexpr int c = K / 2 - 1;
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    double e[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) e[i] = (i == q) ? 1.0 : 0.0;
+    if constexpr (K == 8) om[q] = central8<c>(e);
+    else om[q] = central6<c>(e);
+  }
+}
+
+/* Returns true when omega is exactly the central scheme (every candidate used as it is:
+   smooth, or nonsmooth but left unchanged by the MP median) with the maximal-order d_k. */
 template <int K, int LIM>
-__device__ __forceinline__ void teno_m_weights(const double (&v)[K], unsigned bits, const SchemeDev& S,
+__device__ __forceinline__ bool teno_m_weights(const double (&v)[K], unsigned bits, const SchemeDev& S,
                                                double (&om)[K]) {
   constexpr int c = K / 2 - 1;
   constexpr int nk = K - 2;
 #pragma unroll
   for (int i = 0; i < K; ++i) om[i] = 0.0;
   if (S.weights == W_TENO) {
+    if (bits == (1u << nk) - 1u && S.default_d) {
+      central_weights<K>(om);
+      return true;
+    }
     double den = 0.0;
 #pragma unroll
     for (int k = 0; k < nk; ++k)
@@ -185,9 +204,14 @@ __device__ __forceinline__ void teno_m_weights(const double (&v)[K], unsigned bi
 #pragma unroll
         for (int i = 0; i < K; ++i) om[i] += S.d[k] * rden * g[i];
       }
-    return;
+    return false;
   }
   const bool all = bits == (1u << nk) - 1u;
+  if (all && S.default_d) {  /* sum_k d_k f_k = the central scheme: constant weights */
+    central_weights<K>(om);
+    return true;
+  }
+  bool changed = false;  /* a limiter replaced some candidate */
   Lin<K> fmin, fmax;
   double gt[K];
   if (!all) {
@@ -213,14 +237,17 @@ __device__ __forceinline__ void teno_m_weights(const double (&v)[K], unsigned bi
         const double x = fmin.v - fk, y = fmax.v - fk;
         if (ipos(x) && ipos(y)) {
           const bool ymin = ilt(y, x);
+          changed = true;
 #pragma unroll
           for (int i = 0; i < K; ++i) g[i] = ymin ? fmax.g[i] : fmin.g[i];
         } else if (ineg(x) && ineg(y)) {
           const bool ymax = ilt(x, y);
+          changed = true;
 #pragma unroll
           for (int i = 0; i < K; ++i) g[i] = ymax ? fmax.g[i] : fmin.g[i];
         }
       } else {
+        changed = true;
 #pragma unroll
         for (int i = 0; i < K; ++i) g[i] = gt[i];
       }
@@ -228,15 +255,26 @@ __device__ __forceinline__ void teno_m_weights(const double (&v)[K], unsigned bi
 #pragma unroll
     for (int i = 0; i < K; ++i) om[i] += S.d[k] * g[i];
   }
+  if (!changed && S.default_d) {
+    central_weights<K>(om);
+    return true;
+  }
+  return false;
+}
+
+template <int K>
+__device__ __forceinline__ double central_fn(const double* v) {
+  if constexpr (K == 8) return central8<K / 2 - 1>(v);
+  else return central6<K / 2 - 1>(v);
 }
 
 /* Reverse of the point quantities (stage_point): adjoints of the physical flux F_AXIS (Fb),
    of the velocity (velb), sound speed (cb), enthalpy (Hb) and sqrt(rho) (sb) of one point
    -> adjoint of its conserved state, added to Ub. */
 template <int NV, int AXIS>
-__device__ __forceinline__ void point_vjp(const double* sm, int NP, int p, double gamma, const double (&Fb)[NV],
-                                          double (&velb)[NV - 2], double cb, double Hb, double sb, double* Ub,
-                                          int ustride) {
+__device__ __forceinline__ void point_vjp(const double* sm, const double* rec, int NP, int p, double gamma,
+                                          const double (&Fb)[NV], double (&velb)[NV - 2], double cb, double Hb,
+                                          double sb, double* Ub, int ustride) {
   using L = PointLayout<NV>;
   constexpr int D = NV - 2;
   const double rho = sm[L::cU * NP + p], E = sm[(L::cU + NV - 1) * NP + p];
@@ -248,9 +286,9 @@ __device__ __forceinline__ void point_vjp(const double* sm, int NP, int p, doubl
     ke += m[d] * vel[d];
   }
   const double pr = (gamma - 1.0) * (E - 0.5 * ke);
-  const double H = sm[L::cH * NP + p], c = sm[L::cC * NP + p], srho = sm[L::cS * NP + p];
+  const double H = sm[L::cH * NP + p], c = sm[L::cC * NP + p];
   const double un = vel[AXIS];
-  const double rinv = rcp_nr(rho);
+  const double rinv = rec[p];                 /* 1/rho */
   double rhob = 0.0, Eb = 0.0, pb = 0.0, mb[D];
 #pragma unroll
   for (int d = 0; d < D; ++d) mb[d] = 0.0;
@@ -272,13 +310,11 @@ __device__ __forceinline__ void point_vjp(const double* sm, int NP, int p, doubl
   pb += Hb * rinv;
   rhob -= H * Hb * rinv;
   /* c = sqrt(gamma p / rho) */
-  if (cb != 0.0) {
-    const double k = cb * rcp_nr(2.0 * c * rho);
-    pb += gamma * k;
-    rhob -= c * c * k;
-  }
+  const double k = cb * rec[NP + p];          /* 1/(2 c rho) */
+  pb += gamma * k;
+  rhob -= c * c * k;
   /* sqrt(rho) */
-  if (sb != 0.0) rhob += sb * rcp_nr(2.0 * srho);
+  rhob += sb * rec[2 * NP + p];               /* 1/(2 sqrt(rho)) */
   /* p = (gamma - 1)(E - ke/2), ke = sum m_d vel_d */
   Eb += (gamma - 1.0) * pb;
   const double keb = -0.5 * (gamma - 1.0) * pb;
@@ -305,9 +341,9 @@ __device__ __forceinline__ double dsign(double x) { return ipos(x) ? 1.0 : (ineg
    forward's NV x 2 flag bytes of this face (null: decided again here).  The adjoint of
    stencil point q, component v, is ADDED to Ub[(q * NV + v) * ustride]. */
 template <int NV, int K, int LIM, int AXIS, int LANES>
-__device__ __forceinline__ void face_vjp_smem(const double* sm, int NP, int jf, int lane, double gamma,
-                                              const SchemeDev& sch, const uint8_t* flags, const double (&Fb)[NV],
-                                              double* Ub, int ustride, int& st) {
+__device__ __forceinline__ void face_vjp_smem(const double* sm, const double* rec, int NP, int jf, int lane,
+                                              double gamma, const SchemeDev& sch, const uint8_t* flags,
+                                              const double (&Fb)[NV], double* Ub, int ustride, int& st) {
   using L = PointLayout<NV>;
   constexpr int D = NV - 2;
   constexpr int H = K / 2;
@@ -348,6 +384,21 @@ __device__ __forceinline__ void face_vjp_smem(const double* sm, int NP, int jf, 
   for (int q = 0; q < K; ++q)
 #pragma unroll
     for (int v = 0; v < NV; ++v) Fq[q][v] = 0.0;
+  /* central combination of the point fluxes, for fields smooth on both sides */
+  const unsigned full = (1u << (K - 2)) - 1u;
+  const bool use_fc = sch.default_d;
+  double Fc[NV], accS[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    accS[v] = 0.0;
+    Fc[v] = 0.0;
+    if (use_fc) {
+      double arr[K];
+#pragma unroll
+      for (int q = 0; q < K; ++q) arr[q] = P(L::cF + v, q);
+      Fc[v] = central_fn<K>(arr);
+    }
+  }
 
 #pragma unroll 1
   for (int s = 0; s < NV; ++s) {
@@ -375,16 +426,30 @@ __device__ __forceinline__ void face_vjp_smem(const double* sm, int NP, int jf, 
       l[NV - 1] = 0.0;
     }
     const double ha = 0.5 * ((s == 0) ? a_m : (s == NV - 1 ? a_p : a_0));
-    double W[K], gp[K], vm[K];
+    /* both split sides smooth with the maximal-order weights: f+ + f- = sum_q c_q (g+_q + g-_q)
+       = l . sum_q c_q F_q (the central coefficients are symmetric): no alpha, no W */
+    const bool smooth_lane = flags && use_fc && ((flags[2 * s] & 63u) == full) && ((flags[2 * s + 1] & 63u) == full);
+    /* one path per warp: the general path is exact for smooth fields too */
+    const bool smooth = __all_sync(__activemask(), smooth_lane);
+    double fs = 0.0;
+    bool lin_central = smooth;
+    double W[K], gp[K], vm[K], op[K], omm[K];
+    if (smooth) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) fs = fma(l[v], Fc[v], fs);
+    } else {
 #pragma unroll
     for (int q = 0; q < K; ++q) {
-      double w = l[0] * P(L::cU, q), g = l[0] * P(L::cF, q);
+      double w, g;
+      if (acoustic || s == 1) {
+        w = l[0] * P(L::cU, q);
+        g = l[0] * P(L::cF, q);
 #pragma unroll
-      for (int v = 1; v < NV; ++v) {
-        w = fma(l[v], P(L::cU + v, q), w);
-        g = fma(l[v], P(L::cF + v, q), g);
-      }
-      if (!(acoustic || s == 1)) {  /* the forward's sparse shear projection */
+        for (int v = 1; v < NV; ++v) {
+          w = fma(l[v], P(L::cU + v, q), w);
+          g = fma(l[v], P(L::cF + v, q), g);
+        }
+      } else {  /* the forward's sparse shear projection */
         w = fma(-utt, P(L::cU, q), P(L::cU + 1 + dt, q));
         g = fma(-utt, P(L::cF, q), P(L::cF + 1 + dt, q));
       }
@@ -404,12 +469,13 @@ __device__ __forceinline__ void face_vjp_smem(const double* sm, int NP, int jf, 
       bp = f1 & 63u;
       bm = f2 & 63u;
     }
-    double op[K], omm[K];
-    teno_m_weights<K, LIM>(gp, bp, sch, op);
-    teno_m_weights<K, LIM>(vm, bm, sch, omm);
-    double fs = 0.0;
+    const bool cp = teno_m_weights<K, LIM>(gp, bp, sch, op);
+    const bool cm = teno_m_weights<K, LIM>(vm, bm, sch, omm);
 #pragma unroll
     for (int q = 0; q < K; ++q) fs += op[q] * gp[q] + omm[q] * vm[q];
+    /* both reconstructions are the central scheme: the cheap reverse applies */
+    lin_central = use_fc && __all_sync(__activemask(), cp && cm);
+    }
     /* back-projection F = sum_s r_s fs: adjoint of fs and of r_s */
     double fsb;
     if (acoustic) {
@@ -439,25 +505,47 @@ __device__ __forceinline__ void face_vjp_smem(const double* sm, int NP, int jf, 
       for (int d = 0; d < D; ++d)
         if (d == dt) utb[d] += fs * Fb[NV - 1];
     }
-    /* frozen reconstructions and LLF split: g+ = ha W + G/2, g- = -ha W + G/2 */
-    double hab = 0.0, lb[NV];
-#pragma unroll
-    for (int v = 0; v < NV; ++v) lb[v] = 0.0;
-#pragma unroll
-    for (int q = 0; q < K; ++q) {
-      const double gpb = op[q] * fsb, gmb = omm[K - 1 - q] * fsb;
-      const double Wb = ha * (gpb - gmb), Gb = 0.5 * (gpb + gmb);
-      hab += W[q] * (gpb - gmb);
+    double lb[NV];
+    if (lin_central) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        Ub[(q * NV + v) * ustride] += Wb * l[v];
-        Fq[q][v] += Gb * l[v];
-        lb[v] += Wb * P(L::cU + v, q) + Gb * P(L::cF + v, q);
+        lb[v] = fsb * Fc[v];
+        accS[v] = fma(fsb, l[v], accS[v]);
       }
+    } else {
+      /* frozen reconstructions and LLF split: g+ = ha W + G/2, g- = -ha W + G/2 */
+      double hab = 0.0;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) lb[v] = 0.0;
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        const double gpb = op[q] * fsb, gmb = omm[K - 1 - q] * fsb;
+        const double Wb = ha * (gpb - gmb), Gb = 0.5 * (gpb + gmb);
+        hab += W[q] * (gpb - gmb);
+        if (acoustic || s == 1) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            Ub[(q * NV + v) * ustride] += Wb * l[v];
+            Fq[q][v] += Gb * l[v];
+            lb[v] += Wb * P(L::cU + v, q) + Gb * P(L::cF + v, q);
+          }
+        } else {
+          /* shear wave, l = (-u_t, e_t, 0): only l[0] depends on the Roe state */
+          Ub[(q * NV) * ustride] -= Wb * utt;
+          Fq[q][0] -= Gb * utt;
+#pragma unroll
+          for (int d = 0; d < D; ++d)
+            if (d == dt) {
+              Ub[(q * NV + 1 + d) * ustride] += Wb;
+              Fq[q][1 + d] += Gb;
+            }
+          lb[0] += Wb * P(L::cU, q) + Gb * P(L::cF, q);
+        }
+      }
+      if (s == 0) amb += 0.5 * hab;
+      else if (s == NV - 1) apb += 0.5 * hab;
+      else a0b += 0.5 * hab;
     }
-    if (s == 0) amb += 0.5 * hab;
-    else if (s == NV - 1) apb += 0.5 * hab;
-    else a0b += 0.5 * hab;
     /* left eigenvector -> Roe state */
     if (acoustic) {
       b2b += 0.5 * lb[0];
@@ -482,6 +570,17 @@ __device__ __forceinline__ void face_vjp_smem(const double* sm, int NP, int jf, 
 #pragma unroll
       for (int d = 0; d < D; ++d)
         if (d == dt) utb[d] -= lb[0];
+    }
+  }
+  if (use_fc) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      double e[K];
+#pragma unroll
+      for (int i = 0; i < K; ++i) e[i] = (i == q) ? 1.0 : 0.0;
+      const double cq = central_fn<K>(e);  /* the central coefficient of point q (a constant) */
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Fq[q][v] = fma(cq, accS[v], Fq[q][v]);
     }
   }
   /* ---- Roe average -> the two states of the face ---- */
@@ -530,7 +629,7 @@ __device__ __forceinline__ void face_vjp_smem(const double* sm, int NP, int jf, 
     double Fqq[NV];
 #pragma unroll
     for (int v = 0; v < NV; ++v) Fqq[v] = Fq[q][v];
-    point_vjp<NV, AXIS>(sm, NP, pidx(q), gamma, Fqq, velb, cb, Hb, sb, Ub + (q * NV) * ustride, ustride);
+    point_vjp<NV, AXIS>(sm, rec, NP, pidx(q), gamma, Fqq, velb, cb, Hb, sb, Ub + (q * NV) * ustride, ustride);
   }
 }
 

@@ -26,7 +26,8 @@ struct AdjArgs {
 template <int NV, int K, int AXIS>
 struct AdjTile {
   using F = FaceTile<NV, K, AXIS>;
-  static constexpr size_t SMEM = F::SMEM + sizeof(double) * (size_t)K * NV * F::THREADS;
+  /* point tile + per-point reciprocals (1/rho, 1/(2 c rho), 1/(2 sqrt rho)) + per-face slots */
+  static constexpr size_t SMEM = F::SMEM + sizeof(double) * (3 * (size_t)F::NP + (size_t)K * NV * F::THREADS);
 };
 
 template <int NV, int K, int LIM, int AXIS>
@@ -36,7 +37,8 @@ adj_face_kernel(const AdjArgs A) {
   constexpr int H = T::H;
   constexpr int TH = T::THREADS;
   extern __shared__ double sm[];
-  double* slots = sm + PointLayout<NV>::NC * T::NP;
+  double* rec = sm + PointLayout<NV>::NC * T::NP;
+  double* slots = rec + 3 * T::NP;
   const int tid = threadIdx.x;
   const int na = A.n[AXIS];
   int f0, x0 = 0, o1 = 0, o2 = 0;
@@ -72,6 +74,10 @@ adj_face_kernel(const AdjArgs A) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) u[q] = __ldg(A.U + q * A.ncell + cell);
     stage_point<NV, AXIS>(u, A.gamma, sm, T::NP, p, st);
+    const double c = sm[PointLayout<NV>::cC * T::NP + p], sr = sm[PointLayout<NV>::cS * T::NP + p];
+    rec[p] = rcp_nr(u[0]);
+    rec[T::NP + p] = rcp_nr(2.0 * c * u[0]);
+    rec[2 * T::NP + p] = rcp_nr(2.0 * sr);
   }
 #pragma unroll
   for (int k = 0; k < K * NV; ++k) slots[k * TH + tid] = 0.0;
@@ -102,7 +108,7 @@ adj_face_kernel(const AdjArgs A) {
       else flin = xg + (long long)A.n[0] * (o2 + (long long)A.n[1] * f);
       fl = A.flags + flin * NV * 2;
     }
-    face_vjp_smem<NV, K, LIM, AXIS, T::LANES>(sm, T::NP, jf, lane, A.gamma, A.sch, fl, Fb, slots + tid, TH, st);
+    face_vjp_smem<NV, K, LIM, AXIS, T::LANES>(sm, rec, T::NP, jf, lane, A.gamma, A.sch, fl, Fb, slots + tid, TH, st);
   }
   __syncthreads();
   /* gather: point p (row r, lane) is stencil point q = r - jf of face row jf */
