@@ -480,6 +480,11 @@ def run_batch(args):
         torch.distributed.destroy_process_group()
 
 
+def _linear_tape(S, steps, tape):
+    from paper_2010_13289_gb300.autograd import _use_linear
+    return _use_linear(S, steps, tape)
+
+
 def run_adjoint(args):
     """Adjoint workload: 2D 512^2 broadband field with circular jumps, TENO6-MP, 200 SSP-RK3
     steps at a fixed dt, loss = integral of p over a seeded 64 x 64 window at the end;
@@ -506,6 +511,7 @@ def run_adjoint(args):
     dt = S.max_dt(S.init_state(primd), 0.4).item()
     gam = 1.4
     stream = torch.cuda.current_stream()
+    tape = "linear" if _linear_tape(S, min(every, steps), args.tape) else "flags"
 
     def loss_of(rho0, grad=False):
         pr = primd.clone()
@@ -513,7 +519,7 @@ def run_adjoint(args):
         U0 = S.init_state(pr)
         if grad:
             U0.requires_grad_(True)
-        UN = rollout(U0, S, dt, steps, checkpoint_every=every)
+        UN = rollout(U0, S, dt, steps, checkpoint_every=every, tape=tape)
         rho, mx, my, E = UN[0], UN[1], UN[2], UN[3]
         p = (gam - 1.0) * (E - 0.5 * (mx * mx + my * my) / rho)
         return (p[win] * dx * dx).sum(), U0
@@ -558,6 +564,7 @@ def run_adjoint(args):
            "data": "synthetic (seeded, shaped like the paper's workloads)",
            "config": {"workload": name, "shape": [n, n], "K": K, "limiter": "MP" if lim == 0 else "TVD5",
                       "window": win_n, "checkpoint_every": every, "dt": dt,
+                      "tape": tape,
                       "pass": "backward (frozen-branch adjoint, segment recomputation included)"},
            "adjoint_forward_ratio": bwd_ms / fwd_ms,
            "forward_ms_per_step": fwd_ms / steps, "backward_ms_per_step": bwd_ms / steps,
@@ -580,6 +587,8 @@ def main():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--ref-seconds", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tape", default="auto", choices=["auto", "linear", "flags"],
+                    help="adjoint workloads: tape of the recomputed segments")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -218,7 +218,40 @@ tenom_status tenom_rk3_step_adjoint_tape(tenom_ctx* ctx, const double* U_n, cons
                                          const uint8_t* tape_flags, const double* dt_dev, const double* Ubar_np1,
                                          double* Ubar_n);
 
-/* The same without a caller tape: records the step from U_n internally first. */
+/* ---- linearisation tape (faster reverse, larger tape) ----
+ * The flags tape above makes every adjoint sweep rebuild the frozen linear reconstructions
+ * (projection, limiter selections) from the stage state.  The linearisation tape stores
+ * them instead: per face and characteristic field s (Section 4 projection, Eq. mp_flux
+ * filtering, Eq. reconstuction assembly with w_k = d_k), with the frozen linear weights
+ * op (f+) and om (f-, on the mirrored stencil), W_q = l_s . U_q, G_q = l_s . F_q,
+ *   fs = f+ + f- = sum_q sigma_q G_q + (alpha_s / 2) delta_q W_q,
+ *   sigma_q = (op_q + om_{K-1-q}) / 2,  delta_q = op_q - om_{K-1-q},
+ * the record is (fs, omegaW = sum_q delta_q W_q, sigma_0..K-1, delta_0..K-1): 2K + 2 doubles.
+ * Layout of one stage: axis after axis; inside axis a, [nvar][2K+2][nface_a] doubles
+ * (face order as the face buffers of tenom_face_dump). */
+
+/* Bytes one stage records: sum_a nface_a * nvar * (2K + 2) * 8. */
+size_t tenom_lin_tape_bytes(const tenom_ctx* ctx);
+
+/* dUdt = L(U) as tenom_rhs, also writing the linearisation of L at U to `lin`
+ * (tenom_lin_tape_bytes bytes, caller-owned device memory, 8-byte aligned). */
+tenom_status tenom_rhs_record(tenom_ctx* ctx, const double* U, double* dUdt, double* lin);
+
+/* Ubar = L'(U)^T w from the linearisation tenom_rhs_record wrote at the same U. */
+tenom_status tenom_rhs_vjp_lin(tenom_ctx* ctx, const double* U, const double* lin, const double* w, double* Ubar);
+
+/* tenom_rk3_step recording tape_states = [U1, U2] (as tenom_rk3_step_record) and the
+ * linearisation of its three stages, tape_lin (3 * tenom_lin_tape_bytes bytes). */
+tenom_status tenom_rk3_step_record_lin(tenom_ctx* ctx, double* U, const double* dt_dev, double* tape_states,
+                                       double* tape_lin);
+
+/* As tenom_rk3_step_adjoint_tape, from a step recorded by tenom_rk3_step_record_lin. */
+tenom_status tenom_rk3_step_adjoint_lin(tenom_ctx* ctx, const double* U_n, const double* tape_states,
+                                        const double* tape_lin, const double* dt_dev, const double* Ubar_np1,
+                                        double* Ubar_n);
+
+/* tenom_rk3_step_adjoint_tape without a caller tape: records the step (flags) from U_n
+ * internally first. */
 tenom_status tenom_rk3_step_adjoint(tenom_ctx* ctx, const double* U_n, const double* dt_dev, const double* Ubar_np1,
                                     double* Ubar_n);
 

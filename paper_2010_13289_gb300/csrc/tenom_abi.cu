@@ -420,8 +420,10 @@ static FaceArgs face_args(tenom_ctx* c, const double* U, int axis, double* F, ui
   return a;
 }
 
-static cudaError_t launch_faces(tenom_ctx* c, const double* U, int axis, double* F, uint8_t* flags) {
+static cudaError_t launch_faces(tenom_ctx* c, const double* U, int axis, double* F, uint8_t* flags,
+                                double* lin = nullptr) {
   FaceArgs a = face_args(c, U, axis, F, flags);
+  a.lin = lin;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->timing) {
     while (c->ev.size() < c->ev_used + 2) {
@@ -436,9 +438,15 @@ static cudaError_t launch_faces(tenom_ctx* c, const double* U, int axis, double*
     cudaEventRecord(e0, c->st);
   }
   cudaError_t e;
-  if (c->nv == 3) e = launch_face_nv3(a, axis, c->s.K, c->s.limiter, c->st);
-  else if (c->nv == 4) e = launch_face_nv4(a, axis, c->s.K, c->s.limiter, c->st);
-  else e = launch_face_nv5(a, axis, c->s.K, c->s.limiter, c->st);
+  if (lin) {
+    if (c->nv == 3) e = launch_face_rec_nv3(a, axis, c->s.K, c->s.limiter, c->st);
+    else if (c->nv == 4) e = launch_face_rec_nv4(a, axis, c->s.K, c->s.limiter, c->st);
+    else e = launch_face_rec_nv5(a, axis, c->s.K, c->s.limiter, c->st);
+  } else {
+    if (c->nv == 3) e = launch_face_nv3(a, axis, c->s.K, c->s.limiter, c->st);
+    else if (c->nv == 4) e = launch_face_nv4(a, axis, c->s.K, c->s.limiter, c->st);
+    else e = launch_face_nv5(a, axis, c->s.K, c->s.limiter, c->st);
+  }
   if (c->timing) cudaEventRecord(e1, c->st);
   return e;
 }
@@ -620,13 +628,32 @@ static size_t flags_offset(const tenom_ctx* c, int axis) {
   return b;
 }
 
-static cudaError_t adj_sweeps(tenom_ctx* c, const double* U, const uint8_t* flags_stage, const double* w, double* Z) {
+/* doubles of the linearisation one stage records for one face: NV x (2K + 2) */
+static size_t lin_per_face(const tenom_ctx* c) { return (size_t)c->nv * (2 * c->s.K + 2); }
+
+size_t tenom_lin_tape_bytes(const tenom_ctx* c) {
+  if (!c) return 0;
+  size_t b = 0;
+  for (int a = 0; a < c->g.dim; ++a) b += (size_t)c->nface[a] * lin_per_face(c) * sizeof(double);
+  return b;
+}
+
+/* offset, in doubles, of axis `axis` inside one stage's linearisation */
+static size_t lin_offset(const tenom_ctx* c, int axis) {
+  size_t b = 0;
+  for (int a = 0; a < axis; ++a) b += (size_t)c->nface[a] * lin_per_face(c);
+  return b;
+}
+
+static cudaError_t adj_sweeps(tenom_ctx* c, const double* U, const uint8_t* flags_stage, const double* lin_stage,
+                              const double* w, double* Z) {
   cudaError_t e = cudaMemsetAsync(Z, 0, sizeof(double) * c->nv * c->ncell, c->st);
   for (int a = 0; a < c->g.dim && e == cudaSuccess; ++a) {
     AdjArgs A;
     memset(&A, 0, sizeof(A));
     A.U = U;
     A.flags = flags_stage ? flags_stage + flags_offset(c, a) : nullptr;
+    A.lin = lin_stage ? lin_stage + lin_offset(c, a) : nullptr;
     A.w = w;
     A.Z = Z;
     A.status = c->status;
@@ -635,6 +662,7 @@ static cudaError_t adj_sweeps(tenom_ctx* c, const double* U, const uint8_t* flag
       A.bc[d] = c->g.bc[d];
     }
     A.ncell = c->ncell;
+    A.nface = c->nface[a];
     A.dx = c->g.dx[a];
     A.gamma = c->g.gamma;
     A.sch = scheme_dev(c->s);
@@ -663,18 +691,39 @@ tenom_status tenom_rhs_vjp(tenom_ctx* c, const double* U, const double* w, doubl
   if (!c) return TENOM_E_INVALID;
   if (!aligned8(U) || !aligned8(w) || !aligned8(Ubar) || Ubar == U || Ubar == w)
     return fail(c, TENOM_E_INVALID, "rhs_vjp: bad pointers");
-  cudaError_t e = adj_sweeps(c, U, nullptr, w, Ubar);
+  cudaError_t e = adj_sweeps(c, U, nullptr, nullptr, w, Ubar);
   return e == cudaSuccess ? TENOM_OK : cuda_fail(c, e, "rhs_vjp");
 }
 
-/* one SSP-RK3 step that keeps its stage states and cutoff flags */
-static cudaError_t rk3_record(tenom_ctx* c, double* U, double* U1, double* U2, uint8_t* fl) {
+tenom_status tenom_rhs_record(tenom_ctx* c, const double* U, double* dUdt, double* lin) {
+  if (!c) return TENOM_E_INVALID;
+  if (!aligned8(U) || !aligned8(dUdt) || U == dUdt || !aligned8(lin))
+    return fail(c, TENOM_E_INVALID, "rhs_record: bad pointers");
+  cudaError_t e = cudaSuccess;
+  for (int a = 0; a < c->g.dim && e == cudaSuccess; ++a)
+    e = launch_faces(c, U, a, c->face[a], nullptr, lin + lin_offset(c, a));
+  if (e == cudaSuccess) e = launch_stage(c, nullptr, U, dUdt, 0, 0.0, 0.0);
+  return e == cudaSuccess ? TENOM_OK : cuda_fail(c, e, "rhs_record");
+}
+
+tenom_status tenom_rhs_vjp_lin(tenom_ctx* c, const double* U, const double* lin, const double* w, double* Ubar) {
+  if (!c) return TENOM_E_INVALID;
+  if (!aligned8(U) || !aligned8(lin) || !aligned8(w) || !aligned8(Ubar) || Ubar == U || Ubar == w)
+    return fail(c, TENOM_E_INVALID, "rhs_vjp_lin: bad pointers");
+  cudaError_t e = adj_sweeps(c, U, nullptr, lin, w, Ubar);
+  return e == cudaSuccess ? TENOM_OK : cuda_fail(c, e, "rhs_vjp_lin");
+}
+
+/* one SSP-RK3 step that keeps its stage states and its cutoff flags (fl) or linearisation (lin) */
+static cudaError_t rk3_record(tenom_ctx* c, double* U, double* U1, double* U2, uint8_t* fl, double* lin) {
   const size_t fb = tenom_flags_bytes(c);
+  const size_t lb = tenom_lin_tape_bytes(c) / sizeof(double);
   const double* src[3] = {U, U1, U2};
   cudaError_t e = cudaSuccess;
   for (int st = 0; st < 3 && e == cudaSuccess; ++st) {
     for (int a = 0; a < c->g.dim && e == cudaSuccess; ++a)
-      e = launch_faces(c, src[st], a, c->face[a], fl + st * fb + flags_offset(c, a));
+      e = launch_faces(c, src[st], a, c->face[a], fl ? fl + st * fb + flags_offset(c, a) : nullptr,
+                       lin ? lin + st * lb + lin_offset(c, a) : nullptr);
     if (e != cudaSuccess) break;
     if (st == 0) e = launch_stage(c, nullptr, U, U1, 1, 0.0, 1.0);
     else if (st == 1) e = launch_stage(c, U, U1, U2, 2, 0.75, 0.25);
@@ -683,16 +732,56 @@ static cudaError_t rk3_record(tenom_ctx* c, double* U, double* U1, double* U2, u
   return e;
 }
 
+static tenom_status record_step(tenom_ctx* c, double* U, const double* dt_dev, double* tape_states, uint8_t* fl,
+                                double* lin, const char* what) {
+  cudaError_t e = cudaSuccess;
+  if (dt_dev != c->dt) e = cudaMemcpyAsync(c->dt, dt_dev, sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+  const long long n = c->nv * c->ncell;
+  if (e == cudaSuccess) e = rk3_record(c, U, tape_states, tape_states + n, fl, lin);
+  return e == cudaSuccess ? TENOM_OK : cuda_fail(c, e, what);
+}
+
 tenom_status tenom_rk3_step_record(tenom_ctx* c, double* U, const double* dt_dev, double* tape_states,
                                    uint8_t* tape_flags) {
   if (!c) return TENOM_E_INVALID;
   if (!aligned8(U) || !aligned8(dt_dev) || !aligned8(tape_states) || !tape_flags)
     return fail(c, TENOM_E_INVALID, "rk3_step_record: bad pointers");
-  cudaError_t e = cudaSuccess;
-  if (dt_dev != c->dt) e = cudaMemcpyAsync(c->dt, dt_dev, sizeof(double), cudaMemcpyDeviceToDevice, c->st);
+  return record_step(c, U, dt_dev, tape_states, tape_flags, nullptr, "rk3_step_record");
+}
+
+tenom_status tenom_rk3_step_record_lin(tenom_ctx* c, double* U, const double* dt_dev, double* tape_states,
+                                       double* tape_lin) {
+  if (!c) return TENOM_E_INVALID;
+  if (!aligned8(U) || !aligned8(dt_dev) || !aligned8(tape_states) || !aligned8(tape_lin))
+    return fail(c, TENOM_E_INVALID, "rk3_step_record_lin: bad pointers");
+  return record_step(c, U, dt_dev, tape_states, nullptr, tape_lin, "rk3_step_record_lin");
+}
+
+/* reverse of one recorded step; per stage the sweeps read flags (fl) or the linearisation (lin) */
+static tenom_status adjoint_step(tenom_ctx* c, const double* U_n, const double* tape_states, const uint8_t* fl,
+                                 const double* lin, const double* dt_dev, const double* Ubar_np1, double* Ubar_n) {
+  cudaError_t e = ensure_adj(c);
+  if (e != cudaSuccess) return cuda_fail(c, e, "rk3_step_adjoint");
   const long long n = c->nv * c->ncell;
-  if (e == cudaSuccess) e = rk3_record(c, U, tape_states, tape_states + n, tape_flags);
-  return e == cudaSuccess ? TENOM_OK : cuda_fail(c, e, "rk3_step_record");
+  const size_t fb = tenom_flags_bytes(c);
+  const size_t lb = tenom_lin_tape_bytes(c) / sizeof(double);
+  auto F = [&](int st) { return fl ? fl + st * fb : nullptr; };
+  auto Lz = [&](int st) { return lin ? lin + st * lb : nullptr; };
+  double *A1 = c->adj, *A2 = c->adj + n, *A3 = c->adj + 2 * n, *Z = c->adj + 3 * n;
+  const double *U1 = tape_states, *U2 = tape_states + n;
+  /* stage 3: U^{n+1} = 1/3 U^n + 2/3 (U2 + dt L(U2)) */
+  e = lincomb(c, A1, 2.0 / 3.0, Ubar_np1, 0, nullptr, 0, nullptr, 0, nullptr, nullptr);
+  if (e == cudaSuccess) e = adj_sweeps(c, U2, F(2), Lz(2), A1, Z);
+  if (e == cudaSuccess) e = lincomb(c, A2, 1.0, A1, 0, nullptr, 0, nullptr, 1.0, dt_dev, Z);    /* Ubar2 */
+  /* stage 2: U2 = 3/4 U^n + 1/4 (U1 + dt L(U1)) */
+  if (e == cudaSuccess) e = lincomb(c, A3, 0.25, A2, 0, nullptr, 0, nullptr, 0, nullptr, nullptr);
+  if (e == cudaSuccess) e = adj_sweeps(c, U1, F(1), Lz(1), A3, Z);
+  if (e == cudaSuccess) e = lincomb(c, A3, 1.0, A3, 0, nullptr, 0, nullptr, 1.0, dt_dev, Z);    /* Ubar1 */
+  /* stage 1: U1 = U^n + dt L(U^n) */
+  if (e == cudaSuccess) e = adj_sweeps(c, U_n, F(0), Lz(0), A3, Z);
+  if (e == cudaSuccess)
+    e = lincomb(c, Ubar_n, 1.0 / 3.0, Ubar_np1, 0.75, A2, 1.0, A3, 1.0, dt_dev, Z);
+  return e == cudaSuccess ? TENOM_OK : cuda_fail(c, e, "rk3_step_adjoint");
 }
 
 tenom_status tenom_rk3_step_adjoint_tape(tenom_ctx* c, const double* U_n, const double* tape_states,
@@ -700,27 +789,19 @@ tenom_status tenom_rk3_step_adjoint_tape(tenom_ctx* c, const double* U_n, const 
                                          double* Ubar_n) {
   if (!c) return TENOM_E_INVALID;
   if (!aligned8(U_n) || !aligned8(tape_states) || !tape_flags || !aligned8(dt_dev) || !aligned8(Ubar_np1) ||
-      !aligned8(Ubar_n))
+      !aligned8(Ubar_n) || Ubar_n == Ubar_np1)
     return fail(c, TENOM_E_INVALID, "rk3_step_adjoint: bad pointers");
-  cudaError_t e = ensure_adj(c);
-  if (e != cudaSuccess) return cuda_fail(c, e, "rk3_step_adjoint");
-  const long long n = c->nv * c->ncell;
-  const size_t fb = tenom_flags_bytes(c);
-  double *A1 = c->adj, *A2 = c->adj + n, *A3 = c->adj + 2 * n, *Z = c->adj + 3 * n;
-  const double *U1 = tape_states, *U2 = tape_states + n;
-  /* stage 3: U^{n+1} = 1/3 U^n + 2/3 (U2 + dt L(U2)) */
-  e = lincomb(c, A1, 2.0 / 3.0, Ubar_np1, 0, nullptr, 0, nullptr, 0, nullptr, nullptr);
-  if (e == cudaSuccess) e = adj_sweeps(c, U2, tape_flags + 2 * fb, A1, Z);
-  if (e == cudaSuccess) e = lincomb(c, A2, 1.0, A1, 0, nullptr, 0, nullptr, 1.0, dt_dev, Z);    /* Ubar2 */
-  /* stage 2: U2 = 3/4 U^n + 1/4 (U1 + dt L(U1)) */
-  if (e == cudaSuccess) e = lincomb(c, A3, 0.25, A2, 0, nullptr, 0, nullptr, 0, nullptr, nullptr);
-  if (e == cudaSuccess) e = adj_sweeps(c, U1, tape_flags + fb, A3, Z);
-  if (e == cudaSuccess) e = lincomb(c, A3, 1.0, A3, 0, nullptr, 0, nullptr, 1.0, dt_dev, Z);    /* Ubar1 */
-  /* stage 1: U1 = U^n + dt L(U^n) */
-  if (e == cudaSuccess) e = adj_sweeps(c, U_n, tape_flags, A3, Z);
-  if (e == cudaSuccess)
-    e = lincomb(c, Ubar_n, 1.0 / 3.0, Ubar_np1, 0.75, A2, 1.0, A3, 1.0, dt_dev, Z);
-  return e == cudaSuccess ? TENOM_OK : cuda_fail(c, e, "rk3_step_adjoint");
+  return adjoint_step(c, U_n, tape_states, tape_flags, nullptr, dt_dev, Ubar_np1, Ubar_n);
+}
+
+tenom_status tenom_rk3_step_adjoint_lin(tenom_ctx* c, const double* U_n, const double* tape_states,
+                                        const double* tape_lin, const double* dt_dev, const double* Ubar_np1,
+                                        double* Ubar_n) {
+  if (!c) return TENOM_E_INVALID;
+  if (!aligned8(U_n) || !aligned8(tape_states) || !aligned8(tape_lin) || !aligned8(dt_dev) || !aligned8(Ubar_np1) ||
+      !aligned8(Ubar_n) || Ubar_n == Ubar_np1)
+    return fail(c, TENOM_E_INVALID, "rk3_step_adjoint_lin: bad pointers");
+  return adjoint_step(c, U_n, tape_states, nullptr, tape_lin, dt_dev, Ubar_np1, Ubar_n);
 }
 
 tenom_status tenom_rk3_step_adjoint(tenom_ctx* c, const double* U_n, const double* dt_dev, const double* Ubar_np1,
@@ -734,7 +815,7 @@ tenom_status tenom_rk3_step_adjoint(tenom_ctx* c, const double* U_n, const doubl
   e = cudaMemcpyAsync(Uc, U_n, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->st);
   if (e == cudaSuccess && dt_dev != c->dt)
     e = cudaMemcpyAsync(c->dt, dt_dev, sizeof(double), cudaMemcpyDeviceToDevice, c->st);
-  if (e == cudaSuccess) e = rk3_record(c, Uc, c->adj + 5 * n, c->adj + 6 * n, c->adj_flags);
+  if (e == cudaSuccess) e = rk3_record(c, Uc, c->adj + 5 * n, c->adj + 6 * n, c->adj_flags, nullptr);
   if (e != cudaSuccess) return cuda_fail(c, e, "rk3_step_adjoint");
   return tenom_rk3_step_adjoint_tape(c, U_n, c->adj + 5 * n, c->adj_flags, dt_dev, Ubar_np1, Ubar_n);
 }

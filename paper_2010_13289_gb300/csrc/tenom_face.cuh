@@ -15,6 +15,7 @@
 #pragma once
 #include <cstdint>
 #include "tenom_recon.cuh"
+#include "tenom_linear.cuh"
 #include "tenom_fastmath.cuh"
 
 namespace tenom {
@@ -23,6 +24,7 @@ struct FaceArgs {
   const double* U;    /* [NV][ncell] */
   double* Fhat;       /* [NV][nface] */
   uint8_t* flags;     /* [nface][NV][2] or null */
+  double* lin;        /* linearisation [NV][2K+2][nface] (record kernels only) */
   int* status;        /* sticky status word */
   int n[3];
   int bc[3];
@@ -101,10 +103,16 @@ __device__ __forceinline__ void stage_point(const double (&u)[NV], double gamma,
 /* Flux at the face whose K stencil points are shared-memory points (jf + q) * LANES + lane,
    q = 0..K-1, of a tile laid out by PointLayout<NV> with NP points per component:
    Roe average of points K/2-1 and K/2, characteristic projection, LLF split, TENO-M per
-   field and side, back-projection.  flags (may be null) receives NV x 2 bytes. */
-template <int NV, int K, int LIM, int AXIS, int LANES>
+   field and side, back-projection.  flags (may be null) receives NV x 2 bytes.
+   REC: also write the face's linearisation to lin[j * lstride], j = s * (2K + 2) + ...:
+   per characteristic field s the reconstructed fs = f+ + f-, omegaW = sum_q delta_q W_q,
+   sigma_q (K) and delta_q (K), where with the frozen linear weights op (f+) and om (f-, on
+   the mirrored stencil) fs = sum_q sigma_q G_q + (alpha_s/2) delta_q W_q:
+   sigma_q = (op_q + om_{K-1-q})/2, delta_q = op_q - om_{K-1-q}. */
+template <int NV, int K, int LIM, int AXIS, int LANES, bool REC = false>
 __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf, int lane, double gamma,
-                                               const SchemeDev& sch, double (&Fh)[NV], uint8_t* flags, int& st) {
+                                               const SchemeDev& sch, double (&Fh)[NV], uint8_t* flags, int& st,
+                                               double* lin = nullptr, long long lstride = 0) {
   using L = PointLayout<NV>;
   constexpr int D = NV - 2;
   constexpr int H = K / 2;
@@ -169,7 +177,7 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
     /* characteristic projection of the K stencil points and LLF split
        g+- = (G +- alpha W)/2, evaluated as fma(+-alpha/2, W, G/2) */
     const double ha = 0.5 * ((s == 0) ? a_m : (s == NV - 1 ? a_p : a_0));
-    double gp[K], gm[K];
+    double gp[K], gm[K], Wr[REC ? K : 1];
     if (acoustic || s == 1) {
 #pragma unroll
       for (int q = 0; q < K; ++q) {
@@ -182,6 +190,7 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
         const double hg = 0.5 * g;
         gp[q] = fma(ha, w, hg);
         gm[q] = fma(-ha, w, hg);
+        if constexpr (REC) Wr[q] = w;
       }
     } else {
       /* shear wave: l = (-u_t, e_t, 0) */
@@ -191,6 +200,7 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
         const double hg = 0.5 * fma(-utt, P(L::cF, q), P(L::cF + 1 + dt, q));
         gp[q] = fma(ha, w, hg);
         gm[q] = fma(-ha, w, hg);
+        if constexpr (REC) Wr[q] = w;
       }
     }
     /* f+ on the upwind stencil, f- on the stencil mirrored about x_{i+1/2} */
@@ -205,6 +215,22 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
       flags[s * 2 + 1] = (uint8_t)flm;
     }
     const double fs = fplus + fminus;
+    if constexpr (REC) {
+      double op[K], om[K];
+      teno_m_weights<K, LIM>(gp, flp & 63u, sch, op);
+      teno_m_weights<K, LIM>(vm, flm & 63u, sch, om);
+      double* o = lin + (long long)s * (2 * K + 2) * lstride;
+      double wW = 0.0;
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        const double dq = op[q] - om[K - 1 - q];
+        o[(2 + q) * lstride] = 0.5 * (op[q] + om[K - 1 - q]);
+        o[(2 + K + q) * lstride] = dq;
+        wW = fma(dq, Wr[q], wW);
+      }
+      o[0] = fs;
+      o[lstride] = wW;
+    }
     /* back-projection F += r_s fs */
     if (acoustic) {
       const double sr = -sg;                            /* r: -c for u-c, +c for u+c */
@@ -226,7 +252,7 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
   }
 }
 
-template <int NV, int K, int LIM, int AXIS>
+template <int NV, int K, int LIM, int AXIS, bool REC = false>
 __global__ void __launch_bounds__(FaceTile<NV, K, AXIS>::THREADS)
 face_kernel(const FaceArgs A) {
   using T = FaceTile<NV, K, AXIS>;
@@ -284,8 +310,9 @@ face_kernel(const FaceArgs A) {
     else if (AXIS == 1) flin = xg + (long long)A.n[0] * (f + (long long)(A.n[1] + 1) * o2);
     else flin = xg + (long long)A.n[0] * (o2 + (long long)A.n[1] * f);
     double Fh[NV];
-    face_flux_smem<NV, K, LIM, AXIS, T::LANES>(sm, T::NP, jf, lane, A.gamma, A.sch, Fh,
-                                               A.flags ? A.flags + flin * NV * 2 : nullptr, st);
+    face_flux_smem<NV, K, LIM, AXIS, T::LANES, REC>(sm, T::NP, jf, lane, A.gamma, A.sch, Fh,
+                                                    A.flags ? A.flags + flin * NV * 2 : nullptr, st,
+                                                    REC ? A.lin + flin : nullptr, A.nface);
 #pragma unroll
     for (int v = 0; v < NV; ++v) A.Fhat[v * A.nface + flin] = Fh[v];
   }

@@ -9,6 +9,10 @@ namespace tenom {
 cudaError_t launch_face_nv3(const FaceArgs& a, int axis, int K, int lim, cudaStream_t st);
 cudaError_t launch_face_nv4(const FaceArgs& a, int axis, int K, int lim, cudaStream_t st);
 cudaError_t launch_face_nv5(const FaceArgs& a, int axis, int K, int lim, cudaStream_t st);
+/* The same, also writing the face linearisation to a.lin (record kernels). */
+cudaError_t launch_face_rec_nv3(const FaceArgs& a, int axis, int K, int lim, cudaStream_t st);
+cudaError_t launch_face_rec_nv4(const FaceArgs& a, int axis, int K, int lim, cudaStream_t st);
+cudaError_t launch_face_rec_nv5(const FaceArgs& a, int axis, int K, int lim, cudaStream_t st);
 
 /* Launch geometry of a face sweep (kept in one place for the tests of the host logic). */
 inline void face_grid(int nv, int axis, const int* n, int K, dim3* grid, dim3* block) {
@@ -42,7 +46,8 @@ cudaError_t launch_rhs_divergence(int nv, double* const F[3], const int n[3], co
 
 namespace tenom {
 struct AdjArgs;
-/* Launch the adjoint face sweep of (NV, K, limiter, axis): Z += L_a'(U)^T w. */
+/* Launch the adjoint face sweep of (NV, K, limiter, axis): Z += L_a'(U)^T w, from a.lin (the
+   recorded linearisation) when set, else from a.flags (or branches decided again). */
 cudaError_t launch_adj_nv3(const AdjArgs& a, int axis, int K, int lim, cudaStream_t st);
 cudaError_t launch_adj_nv4(const AdjArgs& a, int axis, int K, int lim, cudaStream_t st);
 cudaError_t launch_adj_nv5(const AdjArgs& a, int axis, int K, int lim, cudaStream_t st);

@@ -1,0 +1,96 @@
+/* Host-side launchers of the face sweeps and their adjoints, templated on the Euler system (NV = 3, 4, 5 for
+ * 1D, 2D, 3D); each tenom_*_nvN.cu file instantiates one NV so the kernels compile in
+ * parallel.  Dynamic shared memory above 48 KB is opted into once per kernel. */
+#pragma once
+#include "tenom_internal.h"
+#include "tenom_adjoint_kernels.cuh"
+
+namespace tenom {
+
+template <class Kern>
+static cudaError_t launch_tile(Kern kern, bool& attr_done, size_t smem, int nv, int axis, const int* n, int K,
+                               cudaStream_t st, const void* args_ptr) {
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  dim3 grid, block;
+  face_grid(nv, axis, n, K, &grid, &block);
+  void* argv[1] = {const_cast<void*>(args_ptr)};
+  return cudaLaunchKernel((const void*)kern, grid, block, argv, smem, st);
+}
+
+/* forward face sweep (REC: also record the linearisation) */
+template <int NV, int K, int LIM, int AXIS, bool REC>
+static cudaError_t launch_face_one(const FaceArgs& a, cudaStream_t st) {
+  static bool attr_done = false;
+  return launch_tile(face_kernel<NV, K, LIM, AXIS, REC>, attr_done, FaceTile<NV, K, AXIS>::SMEM, NV, AXIS, a.n, K, st,
+                     &a);
+}
+
+template <int NV, int AXIS, bool REC>
+static cudaError_t launch_face_axis(const FaceArgs& a, int K, int lim, cudaStream_t st) {
+  if (K == 6) {
+    if (lim == LIM_MP) return launch_face_one<NV, 6, LIM_MP, AXIS, REC>(a, st);
+    if (lim == LIM_TVD5) return launch_face_one<NV, 6, LIM_TVD5, AXIS, REC>(a, st);
+  } else if (K == 8) {
+    if (lim == LIM_MP) return launch_face_one<NV, 8, LIM_MP, AXIS, REC>(a, st);
+    if (lim == LIM_TVD5) return launch_face_one<NV, 8, LIM_TVD5, AXIS, REC>(a, st);
+  }
+  return cudaErrorNotSupported;
+}
+
+template <int NV, bool REC>
+static cudaError_t launch_face_nv(const FaceArgs& a, int axis, int K, int lim, cudaStream_t st) {
+  if (axis == 0) return launch_face_axis<NV, 0, REC>(a, K, lim, st);
+  if constexpr (NV >= 4)
+    if (axis == 1) return launch_face_axis<NV, 1, REC>(a, K, lim, st);
+  if constexpr (NV >= 5)
+    if (axis == 2) return launch_face_axis<NV, 2, REC>(a, K, lim, st);
+  return cudaErrorNotSupported;
+}
+
+/* adjoint sweep with flags (or branches decided again) */
+template <int NV, int K, int LIM, int AXIS>
+static cudaError_t launch_adj_one(const AdjArgs& a, cudaStream_t st) {
+  static bool attr_done = false;
+  return launch_tile(adj_face_kernel<NV, K, LIM, AXIS>, attr_done, AdjTile<NV, K, AXIS>::SMEM, NV, AXIS, a.n, K, st,
+                     &a);
+}
+
+/* adjoint sweep from a recorded linearisation (no limiter dependence) */
+template <int NV, int K, int AXIS>
+static cudaError_t launch_adj_lin_one(const AdjArgs& a, cudaStream_t st) {
+  static bool attr_done = false;
+  return launch_tile(adj_lin_kernel<NV, K, AXIS>, attr_done, AdjLinTile<NV, K, AXIS>::SMEM, NV, AXIS, a.n, K, st, &a);
+}
+
+template <int NV, int AXIS>
+static cudaError_t launch_adj_axis(const AdjArgs& a, int K, int lim, cudaStream_t st) {
+  if (a.lin) {
+    if (K == 6) return launch_adj_lin_one<NV, 6, AXIS>(a, st);
+    if (K == 8) return launch_adj_lin_one<NV, 8, AXIS>(a, st);
+    return cudaErrorNotSupported;
+  }
+  if (K == 6) {
+    if (lim == LIM_MP) return launch_adj_one<NV, 6, LIM_MP, AXIS>(a, st);
+    if (lim == LIM_TVD5) return launch_adj_one<NV, 6, LIM_TVD5, AXIS>(a, st);
+  } else if (K == 8) {
+    if (lim == LIM_MP) return launch_adj_one<NV, 8, LIM_MP, AXIS>(a, st);
+    if (lim == LIM_TVD5) return launch_adj_one<NV, 8, LIM_TVD5, AXIS>(a, st);
+  }
+  return cudaErrorNotSupported;
+}
+
+template <int NV>
+static cudaError_t launch_adj_nv(const AdjArgs& a, int axis, int K, int lim, cudaStream_t st) {
+  if (axis == 0) return launch_adj_axis<NV, 0>(a, K, lim, st);
+  if constexpr (NV >= 4)
+    if (axis == 1) return launch_adj_axis<NV, 1>(a, K, lim, st);
+  if constexpr (NV >= 5)
+    if (axis == 2) return launch_adj_axis<NV, 2>(a, K, lim, st);
+  return cudaErrorNotSupported;
+}
+
+}  // namespace tenom

@@ -76,8 +76,15 @@ def lib():
         L.tenom_rk3_step_record.argtypes = [VP, VP, VP, VP, VP]
         L.tenom_rk3_step_adjoint_tape.argtypes = [VP, VP, VP, VP, VP, VP, VP]
         L.tenom_rk3_step_adjoint.argtypes = [VP, VP, VP, VP, VP]
+        L.tenom_lin_tape_bytes.argtypes = [VP]
+        L.tenom_lin_tape_bytes.restype = ctypes.c_size_t
+        L.tenom_rhs_record.argtypes = [VP, VP, VP, VP]
+        L.tenom_rhs_vjp_lin.argtypes = [VP, VP, VP, VP, VP]
+        L.tenom_rk3_step_record_lin.argtypes = [VP, VP, VP, VP, VP]
+        L.tenom_rk3_step_adjoint_lin.argtypes = [VP, VP, VP, VP, VP, VP, VP]
         for name in ("tenom_rhs_vjp", "tenom_rk3_step_record", "tenom_rk3_step_adjoint_tape",
-                     "tenom_rk3_step_adjoint"):
+                     "tenom_rk3_step_adjoint", "tenom_rhs_record", "tenom_rhs_vjp_lin",
+                     "tenom_rk3_step_record_lin", "tenom_rk3_step_adjoint_lin"):
             getattr(L, name).restype = c_int
         L.tenom_check_fastmath.argtypes = [VP, VP, ctypes.c_longlong, VP]
         L.tenom_check_fastmath.restype = c_int
@@ -154,6 +161,13 @@ def _ptr(t):
 def _stream():
     import torch
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Tape:
+    """Device tape of one recorded SSP-RK3 step (see Solver.new_tape)."""
+
+    def __init__(self, states, data, linear):
+        self.states, self.data, self.linear = states, data, linear
 
 
 class Solver:
@@ -267,24 +281,58 @@ class Solver:
         self._check(lib().tenom_rhs_vjp(self._ctx, _ptr(U), _ptr(w), _ptr(out)), "tenom_rhs_vjp")
         return out
 
-    def new_tape(self):
+    def lin_tape_bytes(self):
+        """Bytes of the linearisation one operator evaluation records."""
+        return int(lib().tenom_lin_tape_bytes(self._ctx))
+
+    def rhs_record(self, U, lin, out=None):
+        """L(U), also recording its linearisation into `lin` (lin_tape_bytes() bytes)."""
+        out = self.tensor() if out is None else out
+        self._check(lib().tenom_rhs_record(self._ctx, _ptr(U), _ptr(out), _ptr(lin)), "tenom_rhs_record")
+        return out
+
+    def rhs_vjp_lin(self, U, lin, w, out=None):
+        """L'(U)^T w from the linearisation rhs_record wrote at U."""
+        out = self.tensor() if out is None else out
+        self._check(lib().tenom_rhs_vjp_lin(self._ctx, _ptr(U), _ptr(lin), _ptr(w), _ptr(out)), "tenom_rhs_vjp_lin")
+        return out
+
+    def new_lin(self):
+        import torch
+        return torch.empty(self.lin_tape_bytes() // 8, dtype=torch.float64, device="cuda")
+
+    def tape_bytes(self, linear=False):
+        """Device bytes of one step's tape (stage states + flags or linearisation)."""
+        per_stage = self.lin_tape_bytes() if linear else self.flags_bytes()
+        return 2 * 8 * self.nv * int(math.prod(self.shape)) + 3 * per_stage
+
+    def new_tape(self, linear=False):
+        """Tape of one SSP-RK3 step: the stage states U1, U2 and, per stage, the cutoff flags
+        (compact; the reverse rebuilds the frozen reconstructions) or the linearisation
+        (linear=True: larger; the reverse reads it)."""
         import torch
         states = torch.empty((2,) + self.state_shape, dtype=torch.float64, device="cuda")
-        flags = torch.empty(3 * self.flags_bytes(), dtype=torch.uint8, device="cuda")
-        return states, flags
+        if linear:
+            return Tape(states, torch.empty(3 * self.lin_tape_bytes() // 8, dtype=torch.float64, device="cuda"), True)
+        return Tape(states, torch.empty(3 * self.flags_bytes(), dtype=torch.uint8, device="cuda"), False)
 
     def rk3_step_record(self, U, dt_dev, tape):
-        states, flags = tape
-        self._check(lib().tenom_rk3_step_record(self._ctx, _ptr(U), _ptr(dt_dev), _ptr(states), _ptr(flags)),
-                    "tenom_rk3_step_record")
+        if tape.linear:
+            st = lib().tenom_rk3_step_record_lin(self._ctx, _ptr(U), _ptr(dt_dev), _ptr(tape.states), _ptr(tape.data))
+        else:
+            st = lib().tenom_rk3_step_record(self._ctx, _ptr(U), _ptr(dt_dev), _ptr(tape.states), _ptr(tape.data))
+        self._check(st, "tenom_rk3_step_record")
         return U
 
     def rk3_step_adjoint(self, U_n, dt_dev, Ubar_np1, tape=None, out=None):
         out = self.tensor() if out is None else out
         if tape is None:
             st = lib().tenom_rk3_step_adjoint(self._ctx, _ptr(U_n), _ptr(dt_dev), _ptr(Ubar_np1), _ptr(out))
+        elif tape.linear:
+            st = lib().tenom_rk3_step_adjoint_lin(self._ctx, _ptr(U_n), _ptr(tape.states), _ptr(tape.data),
+                                                  _ptr(dt_dev), _ptr(Ubar_np1), _ptr(out))
         else:
-            st = lib().tenom_rk3_step_adjoint_tape(self._ctx, _ptr(U_n), _ptr(tape[0]), _ptr(tape[1]),
+            st = lib().tenom_rk3_step_adjoint_tape(self._ctx, _ptr(U_n), _ptr(tape.states), _ptr(tape.data),
                                                    _ptr(dt_dev), _ptr(Ubar_np1), _ptr(out))
         self._check(st, "tenom_rk3_step_adjoint")
         return out

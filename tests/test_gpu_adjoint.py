@@ -64,6 +64,30 @@ def test_rhs_vjp_dot_product_vs_dual_oracle(T, orc, shape, bc, K, lim, seed):
     assert abs(lhs - rhs) <= 1e-10 * scale, (lhs, rhs, scale)
 
 
+@pytest.mark.parametrize("shape,bc,K,lim,seed", CASES)
+def test_rhs_vjp_from_linearisation_vs_dual_oracle(T, orc, shape, bc, K, lim, seed):
+    """The linearisation tape: rhs_record gives the forward's L(U) and a tape from which
+    rhs_vjp_lin is the same L'^T w (dot-product identity against the dual-number oracle,
+    and against the flags path, which rebuilds the reconstructions, to rounding)."""
+    S, g, so, Uo, Ug = setup(T, orc, shape, bc, K, lim, seed)
+    assert flags_agree(S, orc, g, so, Uo, Ug)
+    lin = S.new_lin()
+    R = S.rhs_record(Ug, lin)
+    np.testing.assert_allclose(R.cpu().numpy(), S.rhs(Ug).cpu().numpy(), rtol=1e-13, atol=1e-13)
+    rng = np.random.default_rng(seed)
+    v = rng.normal(size=Uo.shape)
+    w = rng.normal(size=Uo.shape)
+    _, Jv, bad = orc.rhs_jvp(g, so, Uo, v)
+    assert bad == 0
+    wt = torch.from_numpy(w).cuda()
+    JTw = S.rhs_vjp_lin(Ug, lin, wt).cpu().numpy()
+    lhs, rhs = float(np.sum(w * Jv)), float(np.sum(JTw * v))
+    scale = float(np.sum(np.abs(w * Jv)))
+    assert abs(lhs - rhs) <= 1e-10 * scale, (lhs, rhs, scale)
+    JTw_flags = S.rhs_vjp(Ug, wt).cpu().numpy()
+    assert np.max(np.abs(JTw - JTw_flags)) <= 1e-11 * np.max(np.abs(JTw_flags))
+
+
 @pytest.mark.parametrize("shape,bc,K,lim,seed", CASES[:1] + CASES[3:4] + CASES[4:5] + CASES[5:6])
 def test_rk3_step_adjoint_vs_dual_oracle(T, orc, shape, bc, K, lim, seed):
     S, g, so, Uo, Ug = setup(T, orc, shape, bc, K, lim, seed)
@@ -80,13 +104,22 @@ def test_rk3_step_adjoint_vs_dual_oracle(T, orc, shape, bc, K, lim, seed):
     S.rk3_step_record(U1, dt_dev, tape)
     JTu2 = S.rk3_step_adjoint(Ug, dt_dev, torch.from_numpy(ub).cuda(), tape=tape).cpu().numpy()
     np.testing.assert_allclose(JTu2, JTu, rtol=1e-13, atol=1e-14)
-    lhs, rhs = float(np.sum(ub * Jv)), float(np.sum(JTu * v))
-    scale = float(np.sum(np.abs(ub * Jv)))
-    assert abs(lhs - rhs) <= 1e-10 * scale, (lhs, rhs, scale)
+    # the linearisation tape: same step, same adjoint to rounding
+    tl = S.new_tape(linear=True)
+    U2 = Ug.clone()
+    S.rk3_step_record(U2, dt_dev, tl)
+    np.testing.assert_allclose(U2.cpu().numpy(), U1.cpu().numpy(), rtol=1e-13, atol=1e-13)
+    JTu3 = S.rk3_step_adjoint(Ug, dt_dev, torch.from_numpy(ub).cuda(), tape=tl).cpu().numpy()
+    assert np.max(np.abs(JTu3 - JTu)) <= 1e-11 * np.max(np.abs(JTu))
+    for J in (JTu, JTu3):
+        lhs, rhs = float(np.sum(ub * Jv)), float(np.sum(J * v))
+        scale = float(np.sum(np.abs(ub * Jv)))
+        assert abs(lhs - rhs) <= 1e-10 * scale, (lhs, rhs, scale)
 
 
-def test_rollout_autograd_with_checkpoints_vs_dual_oracle(T, orc):
-    """torch.autograd through a 7-step rollout checkpointed every 3 steps."""
+@pytest.mark.parametrize("tape", ["flags", "linear"])
+def test_rollout_autograd_with_checkpoints_vs_dual_oracle(T, orc, tape):
+    """torch.autograd through a 7-step rollout checkpointed every 3 steps, with either tape."""
     from paper_2010_13289_gb300.autograd import rollout
     shape, bc, K, lim, seed = (24, 20), (0, 0), 6, 0, 4
     S, g, so, Uo, Ug = setup(T, orc, shape, bc, K, lim, seed)
@@ -99,7 +132,7 @@ def test_rollout_autograd_with_checkpoints_vs_dual_oracle(T, orc):
     for _ in range(nsteps):
         U, dU, _ = orc.rk3_step_jvp(g, so, U, dU, dt)
     U0 = Ug.clone().requires_grad_(True)
-    UN = rollout(U0, S, dt, nsteps, checkpoint_every=3)
+    UN = rollout(U0, S, dt, nsteps, checkpoint_every=3, tape=tape)
     np.testing.assert_allclose(UN.detach().cpu().numpy(), U, rtol=1e-11, atol=1e-12)
     loss = (UN * torch.from_numpy(c).cuda()).sum()
     loss.backward()
@@ -152,19 +185,35 @@ def lattice_fd_check(S, U, fwd, vjp, radius, spacing, seed, eps=(1e-7, 2e-8), bo
 
 
 @pytest.mark.parametrize("circles", [4, 0])
-def test_operator_and_step_adjoint_vs_central_differences(T, circles):
+@pytest.mark.parametrize("linear", [False, True])
+def test_operator_and_step_adjoint_vs_central_differences(T, circles, linear):
     """Central differences of the GPU forward against the adjoint, cell by cell away from
     switch faces, to 1e-6 relative: the operator L (support radius 3) and one SSP-RK3
-    step (radius 9), on the broadband field with and without circular jumps."""
+    step (radius 9), on the broadband field with and without circular jumps; reverse from
+    the flags or from the linearisation tape."""
     n = 128
     prim, dx = PB.broadband_2d(n, 5, kmax=8, ncircle=circles)
     S = T.Solver((n, n), (dx, dx), (0, 0), T.make_scheme(6))
     U = S.init_state(torch.from_numpy(prim).cuda())
-    cells, good, worst = lattice_fd_check(S, U, S.rhs, S.rhs_vjp, 3, 8, 1 + circles)
+
+    def op_vjp(X, w):
+        if not linear:
+            return S.rhs_vjp(X, w)
+        lin = S.new_lin()
+        S.rhs_record(X, lin)
+        return S.rhs_vjp_lin(X, lin, w)
+
+    def step_vjp(X, w):
+        if not linear:
+            return S.rk3_step_adjoint(X, dt, w)
+        tape = S.new_tape(linear=True)
+        S.rk3_step_record(X.clone(), dt, tape)
+        return S.rk3_step_adjoint(X, dt, w, tape=tape)
+
+    cells, good, worst = lattice_fd_check(S, U, S.rhs, op_vjp, 3, 8, 1 + circles)
     assert good >= 0.8 * cells and worst <= 1e-6, (cells, good, worst)
     dt = torch.tensor([S.max_dt(U, 0.4).item()], dtype=torch.float64, device="cuda")
-    cells, good, worst = lattice_fd_check(S, U, lambda X: S.rk3_step(X, dt),
-                                          lambda X, w: S.rk3_step_adjoint(X, dt, w), 9, 20, 2 + circles, box=True)
+    cells, good, worst = lattice_fd_check(S, U, lambda X: S.rk3_step(X, dt), step_vjp, 9, 20, 2 + circles, box=True)
     assert good >= 0.8 * cells and worst <= 1e-6, (cells, good, worst)
 
 
