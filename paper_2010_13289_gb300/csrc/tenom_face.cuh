@@ -208,17 +208,15 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
 #pragma unroll
     for (int q = 0; q < K; ++q) vm[q] = gm[K - 1 - q];
     unsigned flp, flm;
-    const double fplus = teno_m<K, LIM>(gp, sch, flp, st);
-    const double fminus = teno_m<K, LIM>(vm, sch, flm, st);
+    double op[REC ? K : 1], om[REC ? K : 1];
+    const double fplus = teno_m<K, LIM, REC>(gp, sch, flp, st, op);
+    const double fminus = teno_m<K, LIM, REC>(vm, sch, flm, st, om);
     if (flags) {
       flags[s * 2 + 0] = (uint8_t)flp;
       flags[s * 2 + 1] = (uint8_t)flm;
     }
     const double fs = fplus + fminus;
     if constexpr (REC) {
-      double op[K], om[K];
-      teno_m_weights<K, LIM>(gp, flp & 63u, sch, op);
-      teno_m_weights<K, LIM>(vm, flm & 63u, sch, om);
       double* o = lin + (long long)s * (2 * K + 2) * lstride;
       double wW = 0.0;
 #pragma unroll

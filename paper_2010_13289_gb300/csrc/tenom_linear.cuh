@@ -138,39 +138,6 @@ __device__ __forceinline__ void tvd5_lin(const double* v, double* g) {
   }
 }
 
-/* Table 1 coefficients on v (index c = f_i) */
-template <int K>
-__device__ __forceinline__ void cand_coeffs(int k, double* g) {
-  constexpr int c = K / 2 - 1;
-#pragma unroll
-  for (int i = 0; i < K; ++i) g[i] = 0.0;
-  switch (k) {
-    case 0: g[c - 1] = -1.0 / 6.0; g[c] = 5.0 / 6.0; g[c + 1] = 2.0 / 6.0; break;
-    case 1: g[c] = 2.0 / 6.0; g[c + 1] = 5.0 / 6.0; g[c + 2] = -1.0 / 6.0; break;
-    case 2: g[c - 2] = 2.0 / 6.0; g[c - 1] = -7.0 / 6.0; g[c] = 11.0 / 6.0; break;
-    case 3: g[c] = 3.0 / 12.0; g[c + 1] = 13.0 / 12.0; g[c + 2] = -5.0 / 12.0; g[c + 3] = 1.0 / 12.0; break;
-    case 4: g[c - 3] = -3.0 / 12.0; g[c - 2] = 13.0 / 12.0; g[c - 1] = -23.0 / 12.0; g[c] = 25.0 / 12.0; break;
-    default:
-      g[c] = 12.0 / 60.0; g[c + 1] = 77.0 / 60.0; g[c + 2] = -43.0 / 60.0; g[c + 3] = 17.0 / 60.0;
-      g[c + 4] = -3.0 / 60.0;
-      break;
-  }
-}
-
-/* omega with fhat = sum_q omega_q v_q under the frozen flags (delta bits in `bits`) */
-template <int K>
-__device__ __forceinline__ void central_weights(double (&om)[K]) {
-  constexpr int c = K / 2 - 1;
-#pragma unroll
-  for (int q = 0; q < K; ++q) {
-    double e[K];
-#pragma unroll
-    for (int i = 0; i < K; ++i) e[i] = (i == q) ? 1.0 : 0.0;
-    if constexpr (K == 8) om[q] = central8<c>(e);
-    else om[q] = central6<c>(e);
-  }
-}
-
 /* Returns true when omega is exactly the central scheme (every candidate used as it is:
    smooth, or nonsmooth but left unchanged by the MP median) with the maximal-order d_k. */
 template <int K, int LIM>

@@ -46,56 +46,144 @@ struct SchemeDev {
 __device__ __forceinline__ double dmin(double a, double b) { return imin(a, b); }
 __device__ __forceinline__ double dmax(double a, double b) { return imax(a, b); }
 
-/* minmod of two arguments (Eq. minmod222; zero if an argument is zero). */
+/* minmod of two arguments (Eq. minmod222; zero if an argument is zero); k receives which
+   argument was taken (0: x, 1: y, -1: zero). */
+__device__ __forceinline__ double minmod2(double x, double y, int& k) {
+  k = -1;
+  if (ipos(x) && ipos(y)) {
+    k = ilt(y, x) ? 1 : 0;
+    return k ? y : x;
+  }
+  if (ineg(x) && ineg(y)) {
+    k = ilt(x, y) ? 1 : 0;
+    return k ? y : x;
+  }
+  return 0.0;
+}
 __device__ __forceinline__ double minmod2(double x, double y) {
-  if (ipos(x) && ipos(y)) return imin(x, y);
-  if (ineg(x) && ineg(y)) return imax(x, y);
+  int k;
+  return minmod2(x, y, k);
+}
+
+/* minmod of four arguments (Eq. minmod444); k receives the argument taken (0..3, -1: zero). */
+__device__ __forceinline__ double minmod4(double a, double b, double c, double d, int& k) {
+  k = -1;
+  if (ipos(a) && ipos(b) && ipos(c) && ipos(d)) {
+    const int kab = ilt(b, a) ? 1 : 0, kcd = ilt(d, c) ? 3 : 2;
+    const double ab = kab ? b : a, cd = (kcd == 3) ? d : c;
+    const bool r = ilt(cd, ab);
+    k = r ? kcd : kab;
+    return r ? cd : ab;
+  }
+  if (ineg(a) && ineg(b) && ineg(c) && ineg(d)) {
+    const int kab = ilt(a, b) ? 1 : 0, kcd = ilt(c, d) ? 3 : 2;
+    const double ab = kab ? b : a, cd = (kcd == 3) ? d : c;
+    const bool r = ilt(ab, cd);
+    k = r ? kcd : kab;
+    return r ? cd : ab;
+  }
   return 0.0;
 }
 
-/* minmod of four arguments (Eq. minmod444). */
-__device__ __forceinline__ double minmod4(double a, double b, double c, double d) {
-  if (ipos(a) && ipos(b) && ipos(c) && ipos(d)) return imin(imin(a, b), imin(c, d));
-  if (ineg(a) && ineg(b) && ineg(c) && ineg(d)) return imax(imax(a, b), imax(c, d));
-  return 0.0;
+/* median(x, y, z) = x + minmod(y - x, z - x) (Eq. median); sel receives 0 (x kept),
+   1 (y) or 2 (z) -- the argument whose value the minmod moved x to. */
+__device__ __forceinline__ double median3(double x, double y, double z, int& sel) {
+  int k;
+  const double m = minmod2(y - x, z - x, k);
+  sel = k + 1;
+  return x + m;
+}
+__device__ __forceinline__ double median3(double x, double y, double z) {
+  int sel;
+  return median3(x, y, z, sel);
 }
 
-/* median(x, y, z) = x + minmod(y - x, z - x) (Eq. median). */
-__device__ __forceinline__ double median3(double x, double y, double z) { return x + minmod2(y - x, z - x); }
-
-/* MP bounds f^{L,min}, f^{L,max} at x_{i+1/2} (Eq. value_min_max); c = index of f_i. */
+/* MP bounds f^{L,min}, f^{L,max} at x_{i+1/2} (Eq. value_min_max); c = index of f_i.
+   code receives the selections: [0] of d^{M4}_{i+1/2} and [1] of d^{M4}_{i-1/2} (the minmod
+   argument, -1 zero; the 2-argument curvature maps d_i / d_{i+1} to 2 / 3), [2] of f^min
+   and [3] of f^max (0 f_i, 1 f_{i+1}, 2 f^MD, 3 f^UL, 4 f^LC). */
 template <int c>
-__device__ __forceinline__ void mp_bounds(const double* v, const SchemeDev& S, double& fmin, double& fmax) {
+__device__ __forceinline__ void mp_bounds(const double* v, const SchemeDev& S, double& fmin, double& fmax,
+                                          int (&code)[4]) {
   const double dm1 = v[c] - 2.0 * v[c - 1] + v[c - 2];   /* d_{i-1} (Eq. curvature) */
   const double d0 = v[c + 1] - 2.0 * v[c] + v[c - 1];    /* d_i */
   const double dp1 = v[c + 2] - 2.0 * v[c + 1] + v[c];   /* d_{i+1} */
   double dhp, dhm;
   if (S.mp_curv == CURV_M4) {                            /* Eq. maximal_curvature */
-    dhp = minmod4(4.0 * d0 - dp1, 4.0 * dp1 - d0, d0, dp1);
-    dhm = minmod4(4.0 * dm1 - d0, 4.0 * d0 - dm1, dm1, d0);
+    dhp = minmod4(4.0 * d0 - dp1, 4.0 * dp1 - d0, d0, dp1, code[0]);
+    dhm = minmod4(4.0 * dm1 - d0, 4.0 * d0 - dm1, dm1, d0, code[1]);
   } else {
-    dhp = minmod2(d0, dp1);
-    dhm = minmod2(dm1, d0);
+    int k0, k1;
+    dhp = minmod2(d0, dp1, k0);
+    dhm = minmod2(dm1, d0, k1);
+    code[0] = k0 < 0 ? -1 : k0 + 2;
+    code[1] = k1 < 0 ? -1 : k1 + 2;
   }
   const double fi = v[c], fip = v[c + 1], fim = v[c - 1];
   const double f_ul = fi + S.mp_alpha * (fi - fim);          /* Eq. upper_limiter */
   const double f_md = 0.5 * (fi + fip) - 0.5 * dhp;          /* Eq. median_value */
   const double f_lc = fi + 0.5 * (fi - fim) + S.mp_beta_third * dhm;  /* Eq. large_curvature */
-  fmin = imax(imin(imin(fi, fip), f_md), imin(imin(fi, f_ul), f_lc));
-  fmax = imin(imax(imax(fi, fip), f_md), imax(imax(fi, f_ul), f_lc));
+  /* fmin = max(min(f_i, f_{i+1}, f^MD), min(f_i, f^UL, f^LC)); fmax mirrors it */
+  {
+    const int k1 = ilt(fip, fi) ? 1 : 0;
+    const double t1 = k1 ? fip : fi;
+    const int kL = ilt(f_md, t1) ? 2 : k1;
+    const double L = (kL == 2) ? f_md : t1;
+    const int k2 = ilt(f_ul, fi) ? 3 : 0;
+    const double t2 = k2 ? f_ul : fi;
+    const int kR = ilt(f_lc, t2) ? 4 : k2;
+    const double R = (kR == 4) ? f_lc : t2;
+    const bool r = ilt(L, R);
+    fmin = r ? R : L;
+    code[2] = r ? kR : kL;
+  }
+  {
+    const int k1 = ilt(fi, fip) ? 1 : 0;
+    const double t1 = k1 ? fip : fi;
+    const int kL = ilt(t1, f_md) ? 2 : k1;
+    const double L = (kL == 2) ? f_md : t1;
+    const int k2 = ilt(fi, f_ul) ? 3 : 0;
+    const double t2 = k2 ? f_ul : fi;
+    const int kR = ilt(t2, f_lc) ? 4 : k2;
+    const double R = (kR == 4) ? f_lc : t2;
+    const bool r = ilt(R, L);
+    fmax = r ? R : L;
+    code[3] = r ? kR : kL;
+  }
+}
+template <int c>
+__device__ __forceinline__ void mp_bounds(const double* v, const SchemeDev& S, double& fmin, double& fmax) {
+  int code[4];
+  mp_bounds<c>(v, S, fmin, fmax, code);
 }
 
 /* TVD5 flux f_i + phi delta^-/2 in difference form: with D_m = f_m - f_{m-1} and
    B = (-2 D_{i-1} + 11 D_i + 24 D_{i+1} - 3 D_{i+2})/30, phi delta^- is
-   max(0, min(2D_i, 2D_{i+1}, B)) for D_i > 0, min(0, max(...)) for D_i < 0, 0 for D_i = 0. */
+   max(0, min(2D_i, 2D_{i+1}, B)) for D_i > 0, min(0, max(...)) for D_i < 0, 0 for D_i = 0.
+   pick receives the term taken: 0 (2D_i), 1 (2D_{i+1}), 2 (B), -1 (zero). */
 template <int c>
-__device__ __forceinline__ double tvd5_flux(const double* v) {
+__device__ __forceinline__ double tvd5_flux(const double* v, int& pick) {
   const double Dm = v[c - 1] - v[c - 2], D0 = v[c] - v[c - 1], Dp = v[c + 1] - v[c], Dpp = v[c + 2] - v[c + 1];
   const double B = (-2.0 * Dm + 11.0 * D0 + 24.0 * Dp - 3.0 * Dpp) * (1.0 / 30.0);
   double pd = 0.0;
-  if (ipos(D0)) pd = imax(0.0, imin(imin(2.0 * D0, 2.0 * Dp), B));
-  else if (ineg(D0)) pd = imin(0.0, imax(imax(2.0 * D0, 2.0 * Dp), B));
+  pick = -1;
+  if (ipos(D0)) {
+    int k = ilt(2.0 * Dp, 2.0 * D0) ? 1 : 0;
+    double m = k ? 2.0 * Dp : 2.0 * D0;
+    if (ilt(B, m)) { m = B; k = 2; }
+    if (ilt(0.0, m)) { pd = m; pick = k; }
+  } else if (ineg(D0)) {
+    int k = ilt(2.0 * D0, 2.0 * Dp) ? 1 : 0;
+    double m = k ? 2.0 * Dp : 2.0 * D0;
+    if (ilt(m, B)) { m = B; k = 2; }
+    if (ilt(m, 0.0)) { pd = m; pick = k; }
+  }
   return v[c] + 0.5 * pd;
+}
+template <int c>
+__device__ __forceinline__ double tvd5_flux(const double* v) {
+  int pick;
+  return tvd5_flux<c>(v, pick);
 }
 
 /* Van Albada flux (Eqs. van_Albada_limiter, slop_ratio, vAflux, kappa = 1/3). */
@@ -247,10 +335,105 @@ __device__ __forceinline__ bool cutoff_filter(const double (&D)[K - 1], const Sc
   return true;
 }
 
+/* Candidate k's Table 1 coefficients on v (c = index of f_i), read off the generated
+   candidate formulas applied to unit vectors (compile-time constants for a constant k). */
+template <int K>
+__device__ __forceinline__ void cand_coeffs(int k, double (&g)[K]) {
+  constexpr int c = K / 2 - 1;
+#pragma unroll
+  for (int i = 0; i < K; ++i) {
+    double e[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) e[j] = (j == i) ? 1.0 : 0.0;
+    double x = 0.0;
+    switch (k) {
+      case 0: x = cand0<c>(e); break;
+      case 1: x = cand1<c>(e); break;
+      case 2: x = cand2<c>(e); break;
+      case 3: x = cand3<c>(e); break;
+      case 4: if constexpr (K == 8) x = cand4<c>(e); break;
+      default: if constexpr (K == 8) x = cand5<c>(e); break;
+    }
+    g[i] = x;
+  }
+}
+
+/* the K-point central scheme's coefficients (all candidates smooth, w_k = maximal-order d_k) */
+template <int K>
+__device__ __forceinline__ void central_weights(double* om) {
+  constexpr int c = K / 2 - 1;
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    double e[K];
+#pragma unroll
+    for (int i = 0; i < K; ++i) e[i] = (i == q) ? 1.0 : 0.0;
+    if constexpr (K == 8) om[q] = central8<c>(e);
+    else om[q] = central6<c>(e);
+  }
+}
+
+/* Gradient on v of the MP bound selected by `code` (mp_bounds), with the curvature
+   selections dcode[0] (d^{M4}_{i+1/2} = p0 d_i + p1 d_{i+1}) and dcode[1]
+   (d^{M4}_{i-1/2} = m0 d_{i-1} + m1 d_i). */
+template <int K>
+__device__ __forceinline__ void mp_bound_grad(int code, const int (&dcode)[4], const SchemeDev& S, double (&g)[K]) {
+  constexpr int c = K / 2 - 1;
+  auto first = [](int k) { return k == 0 ? 4.0 : (k == 1 ? -1.0 : (k == 2 ? 1.0 : 0.0)); };
+  auto second = [](int k) { return k == 0 ? -1.0 : (k == 1 ? 4.0 : (k == 3 ? 1.0 : 0.0)); };
+#pragma unroll
+  for (int i = 0; i < K; ++i) g[i] = 0.0;
+  if (code == 0) {
+    g[c] = 1.0;
+  } else if (code == 1) {
+    g[c + 1] = 1.0;
+  } else if (code == 2) {  /* f^MD = (f_i + f_{i+1})/2 - d^{M4}_{i+1/2}/2 */
+    const double p0 = first(dcode[0]), p1 = second(dcode[0]);
+    g[c - 1] = -0.5 * p0;
+    g[c] = 0.5 + p0 - 0.5 * p1;
+    g[c + 1] = 0.5 - 0.5 * p0 + p1;
+    g[c + 2] = -0.5 * p1;
+  } else if (code == 3) {  /* f^UL = f_i + alpha (f_i - f_{i-1}) */
+    g[c - 1] = -S.mp_alpha;
+    g[c] = 1.0 + S.mp_alpha;
+  } else {                 /* f^LC = f_i + (f_i - f_{i-1})/2 + (beta/3) d^{M4}_{i-1/2} */
+    const double b0 = S.mp_beta_third * first(dcode[1]), b1 = S.mp_beta_third * second(dcode[1]);
+    g[c - 2] = b0;
+    g[c - 1] = -0.5 - 2.0 * b0 + b1;
+    g[c] = 1.5 + b0 - 2.0 * b1;
+    g[c + 1] = b1;
+  }
+}
+
+/* Gradient on v of the TVD5 flux with the term `pick` (tvd5_flux) frozen. */
+template <int K>
+__device__ __forceinline__ void tvd5_grad(int pick, double (&g)[K]) {
+  constexpr int c = K / 2 - 1;
+#pragma unroll
+  for (int i = 0; i < K; ++i) g[i] = 0.0;
+  g[c] = 1.0;
+  if (pick == 0) {         /* + D_i */
+    g[c - 1] = -1.0;
+    g[c] = 2.0;
+  } else if (pick == 1) {  /* + D_{i+1} */
+    g[c] = 0.0;
+    g[c + 1] = 1.0;
+  } else if (pick == 2) {  /* + B/2 */
+    g[c - 2] = 2.0 / 60.0;
+    g[c - 1] = -13.0 / 60.0;
+    g[c] = 1.0 - 13.0 / 60.0;
+    g[c + 1] = 27.0 / 60.0;
+    g[c + 2] = -3.0 / 60.0;
+  }
+}
+
 /* One TENO-M reconstruction.  flag receives delta bits | ([beta]-7) << 6; st receives
-   ST_NONFINITE when an indicator is not finite. */
-template <int K, int LIM>
-__device__ __forceinline__ double teno_m(const double (&v)[K], const SchemeDev& S, unsigned& flag, int& st) {
+   ST_NONFINITE when an indicator is not finite.  WT: om also receives the frozen linear
+   weights of this evaluation, fhat = sum_q om_q v_q with this call's cutoff flags and
+   limiter selections (MP or TVD5 only). */
+template <int K, int LIM, bool WT = false>
+__device__ __forceinline__ double teno_m(const double (&v)[K], const SchemeDev& S, unsigned& flag, int& st,
+                                         double* om = nullptr) {
+  static_assert(!WT || LIM == LIM_MP || LIM == LIM_TVD5, "frozen weights: MP or TVD5");
   constexpr int c = K / 2 - 1;  /* index of f_i */
   constexpr int nk = K - 2;
   double D[K - 1];
@@ -295,6 +478,7 @@ __device__ __forceinline__ double teno_m(const double (&v)[K], const SchemeDev& 
   constexpr unsigned all = (1u << nk) - 1u;
   if (bits == all && S.default_d) {
     /* every candidate smooth: sum_k d_k f_k is the K-point central scheme */
+    if constexpr (WT) central_weights<K>(om);
     if constexpr (K == 8) return central8<c>(v);
     else return central6<c>(v);
   }
@@ -311,25 +495,78 @@ __device__ __forceinline__ double teno_m(const double (&v)[K], const SchemeDev& 
 #pragma unroll
     for (int k = 0; k < nk; ++k)
       if (bits >> k & 1u) { num += S.d[k] * fk[k]; den += S.d[k]; }
+    if constexpr (WT) {
+      const double rden = 1.0 / den;
+#pragma unroll
+      for (int i = 0; i < K; ++i) om[i] = 0.0;
+#pragma unroll
+      for (int k = 0; k < nk; ++k) {
+        double g[K];
+        cand_coeffs<K>(k, g);
+        const double wk = (bits >> k & 1u) ? S.d[k] * rden : 0.0;
+#pragma unroll
+        for (int i = 0; i < K; ++i) om[i] = fma(wk, g[i], om[i]);
+      }
+    }
     return num / den;
   }
+  /* per candidate: 0 used as it is, 1 replaced by the first frozen linear form (MP: f^min;
+     TVD5: the TVD5 flux), 2 by the second (MP: f^max) */
+  int sel[nk];
+#pragma unroll
+  for (int k = 0; k < nk; ++k) sel[k] = 0;
+  int code[4] = {-1, -1, -1, -1};
+  int pick = -1;
   if (bits != all) {
     if constexpr (LIM == LIM_MP) {
       double fmin, fmax;
-      mp_bounds<c>(v, S, fmin, fmax);
+      mp_bounds<c>(v, S, fmin, fmax, code);
 #pragma unroll
       for (int k = 0; k < nk; ++k)
-        if (!(bits >> k & 1u)) fk[k] = median3(fk[k], fmin, fmax);
+        if (!(bits >> k & 1u)) fk[k] = median3(fk[k], fmin, fmax, sel[k]);
     } else {
-      const double fl = (LIM == LIM_TVD5) ? tvd5_flux<c>(v) : va_flux<c>(v);
+      const double fl = (LIM == LIM_TVD5) ? tvd5_flux<c>(v, pick) : va_flux<c>(v);
 #pragma unroll
       for (int k = 0; k < nk; ++k)
-        if (!(bits >> k & 1u)) fk[k] = fl;
+        if (!(bits >> k & 1u)) {
+          fk[k] = fl;
+          sel[k] = 1;
+        }
     }
   }
   double f = 0.0;
 #pragma unroll
   for (int k = 0; k < nk; ++k) f += S.d[k] * fk[k];
+  if constexpr (WT) {
+    /* om = sum over unchanged candidates of d_k c_k + D1 grad(form 1) + D2 grad(form 2) */
+    double D1 = 0.0, D2 = 0.0;
+#pragma unroll
+    for (int i = 0; i < K; ++i) om[i] = 0.0;
+#pragma unroll
+    for (int k = 0; k < nk; ++k) {
+      double g[K];
+      cand_coeffs<K>(k, g);
+      const double wk = (sel[k] == 0) ? S.d[k] : 0.0;
+#pragma unroll
+      for (int i = 0; i < K; ++i)
+        if (g[i] != 0.0) om[i] = fma(wk, g[i], om[i]);
+      D1 += (sel[k] == 1) ? S.d[k] : 0.0;
+      D2 += (sel[k] == 2) ? S.d[k] : 0.0;
+    }
+    if (D1 != 0.0 || D2 != 0.0) {
+      double g1[K], g2[K];
+      if constexpr (LIM == LIM_MP) {
+        mp_bound_grad<K>(code[2], code, S, g1);
+        mp_bound_grad<K>(code[3], code, S, g2);
+      } else {
+        tvd5_grad<K>(pick, g1);
+#pragma unroll
+        for (int i = 0; i < K; ++i) g2[i] = 0.0;
+      }
+#pragma unroll
+      for (int i = 0; i < K; ++i) om[i] = fma(D1, g1[i], fma(D2, g2[i], om[i]));
+    }
+  }
   return f;
 }
 
