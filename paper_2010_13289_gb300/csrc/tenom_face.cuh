@@ -44,6 +44,7 @@ struct PointLayout {
 
 constexpr int FX_FACES = 128;  /* faces per CTA, x sweeps */
 constexpr int FT_FACES = 8;    /* faces per CTA along the axis, y/z sweeps (x 32 lanes) */
+constexpr int QSLOTS = 64;     /* reconstruction queue items per warp: two sides x 32 lanes */
 
 template <int NV, int K, int AXIS>
 struct FaceTile {
@@ -55,6 +56,9 @@ struct FaceTile {
   static constexpr int NP = ROWS * LANES;        /* points per tile */
   static constexpr int THREADS = FACES * LANES;
   static constexpr size_t SMEM = sizeof(double) * NC * NP;
+  /* + one reconstruction queue per warp (recon_pair_queued) */
+  static constexpr size_t QDOUBLES = (size_t)(THREADS / 32) * QSLOTS * (K + 2);
+  static constexpr size_t SMEM_Q = SMEM + sizeof(double) * QDOUBLES;
 };
 
 __device__ __forceinline__ int bc_wrap(int j, int n, int bc) {
@@ -100,6 +104,119 @@ __device__ __forceinline__ void stage_point(const double (&u)[NV], double gamma,
   sm[L::cLp * NP + p] = iabs(un + c);
 }
 
+/* Warp work queue for the two reconstructions (f+, f-) of one characteristic field.
+ * After the certified FP32 cutoff decisions, a side whose candidates are all smooth takes
+ * the K-point central formula in its own lane; every other side (nonsmooth candidates, or
+ * decisions the filter could not certify) is queued in shared memory and the warp's
+ * active lanes work through the queue together, so the long general path (FP64 decisions,
+ * candidates, limiter, assembly) runs with full lanes instead of once per side under
+ * divergence.  wq: this warp's queue, QSLOTS items x (K + 2) doubles, component-major
+ * (values, result, header); am: the warp's active lanes.  WT: the frozen linear weights
+ * of each side (teno_general) come back in wp / wm. */
+/* queue item r: the K stencil values and a header (decided flag bits, or undecided) */
+template <int K>
+__device__ __forceinline__ void queue_put(double* wq, int r, const double (&v)[K], bool decided, unsigned flag) {
+#pragma unroll
+  for (int q = 0; q < K; ++q) wq[q * QSLOTS + r] = v[q];
+  wq[(K + 1) * QSLOTS + r] = __longlong_as_double(decided ? (0x100ll | flag) : 0ll);
+}
+
+/* the lanes in am work through queue items 0..n-1: FP64 decisions where undecided, then
+   the general reconstruction; item r's result goes to slot K, its flag byte to slot K + 1 */
+template <int K, int LIM>
+__device__ __forceinline__ void queue_process(double* wq, int n, unsigned am, const SchemeDev& S, int& st) {
+  const unsigned lt = (1u << (threadIdx.x & 31u)) - 1u;
+  const int wl = __popc(am & lt), na = __popc(am);
+  for (int base = 0; base < n; base += na) {
+    const int it = base + wl;
+    if (it < n) {
+      double v[K];
+#pragma unroll
+      for (int q = 0; q < K; ++q) v[q] = wq[q * QSLOTS + it];
+      const long long h = __double_as_longlong(wq[(K + 1) * QSLOTS + it]);
+      unsigned bits = (unsigned)h & 63u;
+      int ex = 7 + (int)((h >> 6) & 3);
+      if (!(h & 0x100ll)) teno_decide_fp64<K>(v, S, bits, ex, st);
+      wq[K * QSLOTS + it] = teno_general<K, LIM>(v, S, bits);
+      wq[(K + 1) * QSLOTS + it] = __longlong_as_double((long long)(bits | ((unsigned)((ex - 7) & 3) << 6)));
+    }
+  }
+}
+
+template <int K, int LIM, bool WT>
+__device__ __forceinline__ void recon_pair_queued(const double (&vp)[K], const double (&vm)[K], const SchemeDev& S,
+                                                  double* wq, unsigned am, double& fp, double& fm, unsigned& flp,
+                                                  unsigned& flm, double* wp, double* wm, int& st) {
+  constexpr unsigned all = (1u << (K - 2)) - 1u;
+  constexpr long long DECIDED = 0x100;
+  unsigned bp = 0, bm = 0;
+  int ep = 7, em = 7;
+  const bool cp = teno_decide_fast<K>(vp, S, bp, ep);
+  const bool cm = teno_decide_fast<K>(vm, S, bm, em);
+  flp = bp | ((unsigned)((ep - 7) & 3) << 6);
+  flm = bm | ((unsigned)((em - 7) & 3) << 6);
+  const bool centp = cp && bp == all && S.default_d, centm = cm && bm == all && S.default_d;
+  fp = 0.0;
+  fm = 0.0;
+  if (centp) fp = teno_central<K, WT>(vp, wp);
+  if (centm) fm = teno_central<K, WT>(vm, wm);
+  const unsigned lane = threadIdx.x & 31u, lt = (1u << lane) - 1u;
+  __syncwarp(am);  /* the previous field's results have been read back */
+  const unsigned mp = __ballot_sync(am, !centp), mm = __ballot_sync(am, !centm);
+  const int np = __popc(mp), n = np + __popc(mm);
+  if (n == 0) return;
+  const int rp = __popc(mp & lt), rm = np + __popc(mm & lt);
+  if (!centp) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) wq[q * QSLOTS + rp] = vp[q];
+    wq[(K + 1) * QSLOTS + rp] = __longlong_as_double(cp ? (DECIDED | flp) : 0ll);
+  }
+  if (!centm) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) wq[q * QSLOTS + rm] = vm[q];
+    wq[(K + 1) * QSLOTS + rm] = __longlong_as_double(cm ? (DECIDED | flm) : 0ll);
+  }
+  __syncwarp(am);
+  const int wl = __popc(am & lt), na = __popc(am);
+  for (int base = 0; base < n; base += na) {
+    const int it = base + wl;
+    if (it < n) {
+      double v[K];
+#pragma unroll
+      for (int q = 0; q < K; ++q) v[q] = wq[q * QSLOTS + it];
+      const long long h = __double_as_longlong(wq[(K + 1) * QSLOTS + it]);
+      unsigned bits = (unsigned)h & 63u;
+      int ex = 7 + (int)((h >> 6) & 3);
+      if (!(h & DECIDED)) teno_decide_fp64<K>(v, S, bits, ex, st);
+      double w[WT ? K : 1];
+      const double f = teno_general<K, LIM, WT>(v, S, bits, w);
+      wq[K * QSLOTS + it] = f;
+      wq[(K + 1) * QSLOTS + it] = __longlong_as_double((long long)(bits | ((unsigned)((ex - 7) & 3) << 6)));
+      if constexpr (WT) {
+#pragma unroll
+        for (int q = 0; q < K; ++q) wq[q * QSLOTS + it] = w[q];
+      }
+    }
+  }
+  __syncwarp(am);
+  if (!centp) {
+    fp = wq[K * QSLOTS + rp];
+    flp = (unsigned)__double_as_longlong(wq[(K + 1) * QSLOTS + rp]);
+    if constexpr (WT) {
+#pragma unroll
+      for (int q = 0; q < K; ++q) wp[q] = wq[q * QSLOTS + rp];
+    }
+  }
+  if (!centm) {
+    fm = wq[K * QSLOTS + rm];
+    flm = (unsigned)__double_as_longlong(wq[(K + 1) * QSLOTS + rm]);
+    if constexpr (WT) {
+#pragma unroll
+      for (int q = 0; q < K; ++q) wm[q] = wq[q * QSLOTS + rm];
+    }
+  }
+}
+
 /* Flux at the face whose K stencil points are shared-memory points (jf + q) * LANES + lane,
    q = 0..K-1, of a tile laid out by PointLayout<NV> with NP points per component:
    Roe average of points K/2-1 and K/2, characteristic projection, LLF split, TENO-M per
@@ -108,11 +225,14 @@ __device__ __forceinline__ void stage_point(const double (&u)[NV], double gamma,
    per characteristic field s the reconstructed fs = f+ + f-, omegaW = sum_q delta_q W_q,
    sigma_q (K) and delta_q (K), where with the frozen linear weights op (f+) and om (f-, on
    the mirrored stencil) fs = sum_q sigma_q G_q + (alpha_s/2) delta_q W_q:
-   sigma_q = (op_q + om_{K-1-q})/2, delta_q = op_q - om_{K-1-q}. */
+   sigma_q = (op_q + om_{K-1-q})/2, delta_q = op_q - om_{K-1-q}.
+   wq (may be null): this warp's reconstruction queue (recon_pair_queued), shared by the
+   lanes in am, which must all make this call; null: each lane reconstructs its own sides. */
 template <int NV, int K, int LIM, int AXIS, int LANES, bool REC = false>
 __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf, int lane, double gamma,
                                                const SchemeDev& sch, double (&Fh)[NV], uint8_t* flags, int& st,
-                                               double* lin = nullptr, long long lstride = 0) {
+                                               double* lin = nullptr, long long lstride = 0, double* wq = nullptr,
+                                               unsigned am = 0u) {
   using L = PointLayout<NV>;
   constexpr int D = NV - 2;
   constexpr int H = K / 2;
@@ -147,6 +267,56 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
 
 #pragma unroll
   for (int v = 0; v < NV; ++v) Fh[v] = 0.0;
+  /* back-projection F += r_s fs (right eigenvector of field s) */
+  auto backproj = [&](int s, double fs) {
+    if ((s == 0) || (s == NV - 1)) {
+      const double sr = (s == 0) ? -1.0 : 1.0;         /* r: -c for u-c, +c for u+c */
+      Fh[0] += fs;
+#pragma unroll
+      for (int d = 0; d < D; ++d) Fh[1 + d] += (ut[d] + (d == AXIS ? sr * ct : 0.0)) * fs;
+      Fh[NV - 1] += (Ht + sr * una * ct) * fs;
+    } else if (s == 1) {
+      Fh[0] += fs;
+#pragma unroll
+      for (int d = 0; d < D; ++d) Fh[1 + d] += ut[d] * fs;
+      Fh[NV - 1] += 0.5 * q2 * fs;
+    } else {
+      const int dt = (s - 2) < AXIS ? (s - 2) : (s - 1);
+#pragma unroll
+      for (int d = 0; d < D; ++d)
+        if (d == dt) {
+          Fh[1 + d] += fs;
+          Fh[NV - 1] += ut[d] * fs;
+        }
+    }
+  };
+  /* Deferred warp queue (forward without recording): the sides that need the general
+     reconstruction are collected over all fields (flushed early only when full) and worked
+     through together; their back-projection and flags follow the flush.  Per (field, side)
+     entry e = 2s + side: qmask bit e, queue index in 6-bit field e of qslot. */
+  constexpr bool DQ = !REC;
+  unsigned qmask = 0u;
+  unsigned long long qslot = 0ull;
+  int nq = 0;
+  double fsr[DQ ? NV : 1];  /* fs per field, back-projected in field order after the last flush */
+#pragma unroll
+  for (int v = 0; v < (DQ ? NV : 1); ++v) fsr[v] = 0.0;
+  auto flush = [&]() {
+    __syncwarp(am);
+    queue_process<K, LIM>(wq, nq, am, sch, st);
+    __syncwarp(am);
+#pragma unroll
+    for (int e = 0; e < 2 * NV; ++e)
+      if (qmask >> e & 1u) {
+        const int r = (int)((qslot >> (6 * e)) & 63ull);
+        if constexpr (DQ) fsr[e >> 1] += wq[K * QSLOTS + r];
+        if (flags) flags[e] = (uint8_t)__double_as_longlong(wq[(K + 1) * QSLOTS + r]);
+      }
+    qmask = 0u;
+    qslot = 0ull;
+    nq = 0;
+    __syncwarp(am);  /* read back before the queue is refilled */
+  };
 
 #pragma unroll 1
   for (int s = 0; s < NV; ++s) {
@@ -209,13 +379,54 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
     for (int q = 0; q < K; ++q) vm[q] = gm[K - 1 - q];
     unsigned flp, flm;
     double op[REC ? K : 1], om[REC ? K : 1];
-    const double fplus = teno_m<K, LIM, REC>(gp, sch, flp, st, op);
-    const double fminus = teno_m<K, LIM, REC>(vm, sch, flm, st, om);
-    if (flags) {
+    double fplus, fminus;
+    if (DQ && wq) {
+      /* certified decisions and central sides in the lane; the rest to the queue */
+      constexpr unsigned all = (1u << (K - 2)) - 1u;
+      unsigned bp = 0, bm = 0;
+      int ep = 7, em = 7;
+      const bool cp = teno_decide_fast<K>(gp, sch, bp, ep);
+      const bool cm = teno_decide_fast<K>(vm, sch, bm, em);
+      const bool centp = cp && bp == all && sch.default_d, centm = cm && bm == all && sch.default_d;
+      fplus = centp ? teno_central<K>(gp) : 0.0;
+      fminus = centm ? teno_central<K>(vm) : 0.0;
+      flp = bp | ((unsigned)((ep - 7) & 3) << 6);
+      flm = bm | ((unsigned)((em - 7) & 3) << 6);
+      if (flags) {
+        if (centp) flags[s * 2 + 0] = (uint8_t)flp;
+        if (centm) flags[s * 2 + 1] = (uint8_t)flm;
+      }
+      const unsigned lt = (1u << (threadIdx.x & 31u)) - 1u;
+      const unsigned mp = __ballot_sync(am, !centp), mm = __ballot_sync(am, !centm);
+      const int cnt = __popc(mp) + __popc(mm);
+      if (nq + cnt > QSLOTS) flush();
+      const int rp = nq + __popc(mp & lt), rm = nq + __popc(mp) + __popc(mm & lt);
+      if (!centp) {
+        queue_put<K>(wq, rp, gp, cp, flp);
+        qmask |= 1u << (2 * s);
+        qslot |= (unsigned long long)rp << (12 * s);
+      }
+      if (!centm) {
+        queue_put<K>(wq, rm, vm, cm, flm);
+        qmask |= 2u << (2 * s);
+        qslot |= (unsigned long long)rm << (12 * s + 6);
+      }
+      nq += cnt;
+    } else if (wq) {
+      recon_pair_queued<K, LIM, REC>(gp, vm, sch, wq, am, fplus, fminus, flp, flm, op, om, st);
+    } else {
+      fplus = teno_m<K, LIM, REC>(gp, sch, flp, st, op);
+      fminus = teno_m<K, LIM, REC>(vm, sch, flm, st, om);
+    }
+    if (flags && !(DQ && wq)) {
       flags[s * 2 + 0] = (uint8_t)flp;
       flags[s * 2 + 1] = (uint8_t)flm;
     }
     const double fs = fplus + fminus;
+    if (DQ && wq) {
+      if constexpr (DQ) fsr[s] = fs;  /* central sides now, queued sides at the flush */
+      continue;
+    }
     if constexpr (REC) {
       double* o = lin + (long long)s * (2 * K + 2) * lstride;
       double wW = 0.0;
@@ -229,24 +440,13 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
       o[0] = fs;
       o[lstride] = wW;
     }
-    /* back-projection F += r_s fs */
-    if (acoustic) {
-      const double sr = -sg;                            /* r: -c for u-c, +c for u+c */
-      Fh[0] += fs;
+    backproj(s, fs);
+  }
+  if (DQ && wq) {
+    if (nq > 0) flush();
 #pragma unroll
-      for (int d = 0; d < D; ++d) Fh[1 + d] += (ut[d] + (d == AXIS ? sr * ct : 0.0)) * fs;
-      Fh[NV - 1] += (Ht + sr * una * ct) * fs;
-    } else if (s == 1) {
-      Fh[0] += fs;
-#pragma unroll
-      for (int d = 0; d < D; ++d) Fh[1 + d] += ut[d] * fs;
-      Fh[NV - 1] += 0.5 * q2 * fs;
-    } else {
-#pragma unroll
-      for (int d = 0; d < D; ++d)
-        if (d == dt) Fh[1 + d] += fs;
-      Fh[NV - 1] += utt * fs;
-    }
+    for (int s = 0; s < NV; ++s)
+      if constexpr (DQ) backproj(s, fsr[s]);
   }
 }
 
@@ -301,6 +501,7 @@ face_kernel(const FaceArgs A) {
   const int f = f0 + jf;
   const int xg = x0 + lane;
   bool active = (f <= na) && (AXIS == 0 || xg < A.n[0]);
+  const unsigned am = __ballot_sync(0xffffffffu, active);  /* the lanes sharing the warp's queue */
   if (active) {
     /* face linear index (n_a + 1 entries along the axis) */
     long long flin;
@@ -310,7 +511,10 @@ face_kernel(const FaceArgs A) {
     double Fh[NV];
     face_flux_smem<NV, K, LIM, AXIS, T::LANES, REC>(sm, T::NP, jf, lane, A.gamma, A.sch, Fh,
                                                     A.flags ? A.flags + flin * NV * 2 : nullptr, st,
-                                                    REC ? A.lin + flin : nullptr, A.nface);
+                                                    REC ? A.lin + flin : nullptr, A.nface,
+                                                    (REC || K == 6) ? sm + T::NC * T::NP + (size_t)(tid >> 5) * QSLOTS * (K + 2)
+                                                                    : nullptr,
+                                                    am);
 #pragma unroll
     for (int v = 0; v < NV; ++v) A.Fhat[v * A.nface + flin] = Fh[v];
   }

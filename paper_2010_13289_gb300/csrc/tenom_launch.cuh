@@ -25,8 +25,8 @@ static cudaError_t launch_tile(Kern kern, bool& attr_done, size_t smem, int nv, 
 template <int NV, int K, int LIM, int AXIS, bool REC>
 static cudaError_t launch_face_one(const FaceArgs& a, cudaStream_t st) {
   static bool attr_done = false;
-  return launch_tile(face_kernel<NV, K, LIM, AXIS, REC>, attr_done, FaceTile<NV, K, AXIS>::SMEM, NV, AXIS, a.n, K, st,
-                     &a);
+  return launch_tile(face_kernel<NV, K, LIM, AXIS, REC>, attr_done, FaceTile<NV, K, AXIS>::SMEM_Q, NV, AXIS, a.n, K,
+                     st, &a);
 }
 
 template <int NV, int AXIS, bool REC>

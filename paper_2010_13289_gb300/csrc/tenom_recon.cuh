@@ -426,23 +426,17 @@ __device__ __forceinline__ void tvd5_grad(int pick, double (&g)[K]) {
   }
 }
 
-/* One TENO-M reconstruction.  flag receives delta bits | ([beta]-7) << 6; st receives
-   ST_NONFINITE when an indicator is not finite.  WT: om also receives the frozen linear
-   weights of this evaluation, fhat = sum_q om_q v_q with this call's cutoff flags and
-   limiter selections (MP or TVD5 only). */
-template <int K, int LIM, bool WT = false>
-__device__ __forceinline__ double teno_m(const double (&v)[K], const SchemeDev& S, unsigned& flag, int& st,
-                                         double* om = nullptr) {
-  static_assert(!WT || LIM == LIM_MP || LIM == LIM_TVD5, "frozen weights: MP or TVD5");
-  constexpr int c = K / 2 - 1;  /* index of f_i */
+/* Cutoff decisions (delta bits, and [beta] of TENO8A in ex) in FP64: indicators beta_k,
+   beta_K, tau_K, gamma_k and the comparison gamma_k < C_T sum gamma.  st receives
+   ST_NONFINITE when an indicator is not finite. */
+template <int K>
+__device__ __forceinline__ void teno_decide_fp64(const double (&v)[K], const SchemeDev& S, unsigned& bits, int& ex,
+                                                 int& st) {
+  constexpr int c = K / 2 - 1;
   constexpr int nk = K - 2;
   double D[K - 1];
 #pragma unroll
   for (int t = 0; t < K - 1; ++t) D[t] = v[t + 1] - v[t];
-  double fk[nk];
-  unsigned bits = 0;
-  int ex = 7;
-  if (S.exact_decisions || !cutoff_filter<K>(D, S, bits, ex)) {
   double bk[nk];
   bk[0] = beta0<c - 1>(D);
   bk[1] = beta1<c>(D);
@@ -466,6 +460,7 @@ __device__ __forceinline__ double teno_m(const double (&v)[K], const SchemeDev& 
     sum += gk[k];
   }
   double CT = S.ct_const;
+  ex = 7;
   if (S.ct_mode == CT_ADAPTIVE) CT = adaptive_ct<c>(D, &ex);
   /* chi_k < C_T  <=>  gamma_k < C_T sum gamma (all positive: compared as bit patterns) */
   const double thr = CT * sum;
@@ -473,15 +468,43 @@ __device__ __forceinline__ double teno_m(const double (&v)[K], const SchemeDev& 
 #pragma unroll
   for (int k = 0; k < nk; ++k) bits |= (ilt_nonneg(gk[k], thr) ? 0u : 1u) << k;
   if (dbits(sum) >= 0x7ff0000000000000ll) st |= ST_NONFINITE;
-  }
-  flag = bits | ((unsigned)((ex - 7) & 3) << 6);
+}
+
+/* Certified single-precision decisions (cutoff_filter); false: undecided, take the FP64
+   path (always, when the scheme asks for FP64 decisions). */
+template <int K>
+__device__ __forceinline__ bool teno_decide_fast(const double (&v)[K], const SchemeDev& S, unsigned& bits, int& ex) {
+  if (S.exact_decisions) return false;
+  double D[K - 1];
+#pragma unroll
+  for (int t = 0; t < K - 1; ++t) D[t] = v[t + 1] - v[t];
+  return cutoff_filter<K>(D, S, bits, ex);
+}
+
+/* every candidate smooth with the maximal-order d_k: sum_k d_k f_k is the K-point central
+   scheme (WT: its constant weights into om) */
+template <int K, bool WT = false>
+__device__ __forceinline__ double teno_central(const double (&v)[K], double* om = nullptr) {
+  constexpr int c = K / 2 - 1;
+  if constexpr (WT) central_weights<K>(om);
+  if constexpr (K == 8) return central8<c>(v);
+  else return central6<c>(v);
+}
+
+/* Reconstruction with the cutoff decisions `bits` taken: candidates (Table 1), MP or TVD5
+   filtering of the nonsmooth ones (Eq. mp_flux), assembly with w_k = d_k (Eq.
+   reconstuction; with W_TENO the classical renormalised weights).  WT: om also receives
+   the frozen linear weights of this evaluation, fhat = sum_q om_q v_q with these cutoff
+   flags and this call's limiter selections (MP or TVD5 only). */
+template <int K, int LIM, bool WT = false>
+__device__ __forceinline__ double teno_general(const double (&v)[K], const SchemeDev& S, unsigned bits,
+                                               double* om = nullptr) {
+  static_assert(!WT || LIM == LIM_MP || LIM == LIM_TVD5, "frozen weights: MP or TVD5");
+  constexpr int c = K / 2 - 1;  /* index of f_i */
+  constexpr int nk = K - 2;
   constexpr unsigned all = (1u << nk) - 1u;
-  if (bits == all && S.default_d) {
-    /* every candidate smooth: sum_k d_k f_k is the K-point central scheme */
-    if constexpr (WT) central_weights<K>(om);
-    if constexpr (K == 8) return central8<c>(v);
-    else return central6<c>(v);
-  }
+  if (bits == all && S.default_d) return teno_central<K, WT>(v, om);
+  double fk[nk];
   fk[0] = cand0<c>(v);
   fk[1] = cand1<c>(v);
   fk[2] = cand2<c>(v);
@@ -568,6 +591,18 @@ __device__ __forceinline__ double teno_m(const double (&v)[K], const SchemeDev& 
     }
   }
   return f;
+}
+
+/* One TENO-M reconstruction: decisions (certified FP32 filter, FP64 where it cannot decide)
+   then teno_general.  flag receives delta bits | ([beta]-7) << 6. */
+template <int K, int LIM, bool WT = false>
+__device__ __forceinline__ double teno_m(const double (&v)[K], const SchemeDev& S, unsigned& flag, int& st,
+                                         double* om = nullptr) {
+  unsigned bits = 0;
+  int ex = 7;
+  if (!teno_decide_fast<K>(v, S, bits, ex)) teno_decide_fp64<K>(v, S, bits, ex, st);
+  flag = bits | ((unsigned)((ex - 7) & 3) << 6);
+  return teno_general<K, LIM, WT>(v, S, bits, om);
 }
 
 }  // namespace tenom
