@@ -41,6 +41,41 @@ DEFAULT = "broadband_2d_2048_teno6_mp"
 FP64_NOMINAL = 1.25e12  # FLOP/s, GB300 FP64 (an FMA counts 2)
 
 
+FACE_SOURCES = ("tenom_face.cuh", "tenom_recon.cuh", "tenom_linear.cuh", "teno_coeffs.cuh", "tenom_fastmath.cuh",
+                "tenom_launch.cuh")
+
+
+def face_source_hash():
+    """Hash of the sources the face kernel is compiled from (tags the ncu figures)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in FACE_SOURCES:
+        with open(os.path.join(ROOT, "paper_2010_13289_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_figures(name):
+    """ncu figures of the face kernel committed for this workload (profiles/), or None when
+    there are none or they were taken from other kernel sources than the ones built now."""
+    path = os.path.join(ROOT, "profiles", "face_kernel_%s.md" % name)
+    if not os.path.exists(path):
+        return None
+    fig, inside = {}, False
+    for line in open(path):
+        if line.strip() == "```figures":
+            inside = True
+        elif inside and line.strip() == "```":
+            break
+        elif inside and ":" in line:
+            k, v = line.split(":", 1)
+            fig[k.strip()] = v.strip()
+    if fig.get("source_sha256") != face_source_hash():
+        return None
+    fig["file"] = os.path.relpath(path, ROOT)
+    return fig
+
+
 def flops_per_face(name):
     """Stored algorithmic FP64 operation counts per face (oracle op counter)."""
     key = {"broadband_2d_2048_teno6_mp": ("broadband_2d_2048", "K=6", "lim=MP"),
@@ -317,8 +352,22 @@ def run_ours(args):
             "frac": achieved / FP64_NOMINAL if achieved else None, "traffic": None,
             "kernel": "face_kernel (fused characteristic TENO-M face flux)",
             "flops_per_face": fpf, "faces_per_launch": faces_per_launch, "ms_per_launch": face_ms,
-            "launches_timed": face_launches, "peak_note": "nominal GB300 FP64 (FMA = 2 flops)",
+            "launches_timed": face_launches,
+            "peak_note": "nominal GB300 FP64: 2 DFMA lanes/clock/SM x 152 SMs x 2.07 GHz, FMA = 2 flops",
+            "achieved_note": "algorithmic flops = the oracle's per-face count of the textbook method "
+                             "(indicators, comparisons and min/max in FP64); the kernel retires far "
+                             "fewer FP64 operations per face, hence frac > 1",
             "fp64_probe_flops": probe}
+    fig = profile_figures(name)
+    if fig:
+        fpi = float(fig["fp64_thread_instr_per_face"])
+        mhz = clk.get("sm_mhz") or 2070.0
+        roof["traffic"] = float(fig["dram_bytes_per_launch"])
+        roof["executed"] = {
+            "fp64_thread_instr_per_face": fpi, "fp64_pipe_busy_ncu": float(fig["fp64_pipe_busy"]),
+            "frac_fp64_issue": fpi * faces_per_launch / (face_ms * 1e-3) / (304 * mhz * 1e6) if face_ms > 0 else None,
+            "note": "FP64 instructions the kernel executes (ncu, %s) at the live launch time over the "
+                    "FP64 pipe's 304 lanes per clock" % fig["file"]}
     launches_per_step = 3 + 3 * (len(shape) + 1)
 
     out = {"metric": "cell-updates/s per RK stage (FP64)", "value": value, "unit": "cell-updates/s",
@@ -502,6 +551,9 @@ def run_adjoint(args):
     from paper_2010_13289_gb300.autograd import rollout
     name = args.workload
     n, seed, steps, win_n, every, K, lim = ADJOINT_WORKLOADS[name]
+    if args.rollout_steps:  # shorter rollouts for profiling runs (not the workload's number)
+        steps = args.rollout_steps
+    ndirs = args.fd_dirs
     prim, dx = PB.broadband_2d(n, seed)
     rng = np.random.default_rng(seed)
     wy, wx = rng.integers(0, n - win_n, 2)
@@ -548,7 +600,7 @@ def run_adjoint(args):
     rng = np.random.default_rng(seed + 16)
     fd_err = []
     with torch.no_grad():
-        for _ in range(16):
+        for _ in range(ndirs):
             d = torch.from_numpy(rng.normal(size=(n, n))).cuda()
             d /= torch.linalg.norm(d)
             Lp, _ = loss_of(primd[0] + 1e-8 * d)
@@ -569,8 +621,9 @@ def run_adjoint(args):
            "adjoint_forward_ratio": bwd_ms / fwd_ms,
            "forward_ms_per_step": fwd_ms / steps, "backward_ms_per_step": bwd_ms / steps,
            "loss": L.item(), "grad_norm": gnorm,
-           "fd_check": {"directions": 16, "step": 1e-8, "max_err_over_grad_norm": max(fd_err),
-                        "median_err_over_grad_norm": float(np.median(fd_err))},
+           "fd_check": {"directions": ndirs, "step": 1e-8,
+                        "max_err_over_grad_norm": max(fd_err) if fd_err else None,
+                        "median_err_over_grad_norm": float(np.median(fd_err)) if fd_err else None},
            "clocks": clk}
     print(json.dumps(out), flush=True)
     S.close()
@@ -589,6 +642,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tape", default="auto", choices=["auto", "linear", "flags"],
                     help="adjoint workloads: tape of the recomputed segments")
+    ap.add_argument("--rollout-steps", type=int, default=0,
+                    help="adjoint workloads: rollout length (default: the workload's 200); for profiling runs")
+    ap.add_argument("--fd-dirs", type=int, default=16,
+                    help="adjoint workloads: finite-difference directions (default 16)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
