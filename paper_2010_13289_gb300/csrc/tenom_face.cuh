@@ -294,7 +294,7 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
      reconstruction are collected over all fields (flushed early only when full) and worked
      through together; their back-projection and flags follow the flush.  Per (field, side)
      entry e = 2s + side: qmask bit e, queue index in 6-bit field e of qslot. */
-  constexpr bool DQ = !REC;
+  constexpr bool DQ = !REC && K == 6;  /* K = 8: per-field queue (register budget) */
   unsigned qmask = 0u;
   unsigned long long qslot = 0ull;
   int nq = 0;
@@ -512,9 +512,7 @@ face_kernel(const FaceArgs A) {
     face_flux_smem<NV, K, LIM, AXIS, T::LANES, REC>(sm, T::NP, jf, lane, A.gamma, A.sch, Fh,
                                                     A.flags ? A.flags + flin * NV * 2 : nullptr, st,
                                                     REC ? A.lin + flin : nullptr, A.nface,
-                                                    (REC || K == 6) ? sm + T::NC * T::NP + (size_t)(tid >> 5) * QSLOTS * (K + 2)
-                                                                    : nullptr,
-                                                    am);
+                                                    sm + T::NC * T::NP + (size_t)(tid >> 5) * QSLOTS * (K + 2), am);
 #pragma unroll
     for (int v = 0; v < NV; ++v) A.Fhat[v * A.nface + flin] = Fh[v];
   }
