@@ -272,9 +272,10 @@ tenom_status tenom_kernel_timing(tenom_ctx* ctx, int enable, double* face_ms_per
 tenom_status tenom_fp64_peak(void* stream, int nblocks, int iters, double* flops);
 
 /* Numerical self-check (not part of the method): for each x[i] (positive, normal) writes
- * out[5i..5i+4] = (two-step Newton-Raphson 1/x used by the kernels, CUDA's 1.0/x,
+ * out[6i..6i+5] = (two-step Newton-Raphson 1/x used by the kernels, CUDA's 1.0/x,
  * x * Newton 1/sqrt(x) used by the kernels, CUDA's sqrt(x), one-step Newton 1/x used where
- * only a comparison follows).  Device arrays; async. */
+ * only a comparison follows, the kernels' integer-pipe FP32 truncation of x (of -x for odd
+ * i), widened back to double).  Device arrays; async. */
 tenom_status tenom_check_fastmath(const double* x, double* out, long long n, void* stream);
 
 #ifdef __cplusplus

@@ -165,12 +165,13 @@ __global__ void advance_time_kernel(double* t, const double* dt) { *t = *t + *dt
 __global__ void fastmath_check_kernel(const double* x, double* out, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double v = x[i];
-    out[5 * i + 0] = rcp_nr(v);
-    out[5 * i + 1] = 1.0 / v;
+    out[6 * i + 0] = rcp_nr(v);
+    out[6 * i + 1] = 1.0 / v;
     const double r = rsqrt_nr(v);
-    out[5 * i + 2] = v * r;
-    out[5 * i + 3] = sqrt(v);
-    out[5 * i + 4] = rcp_nr1(v);
+    out[6 * i + 2] = v * r;
+    out[6 * i + 3] = sqrt(v);
+    out[6 * i + 4] = rcp_nr1(v);
+    out[6 * i + 5] = (double)f32_rz((i & 1) ? -v : v);
   }
 }
 
@@ -255,6 +256,7 @@ static SchemeDev scheme_dev(const tenom_scheme& s) {
   d.mp_beta_third = s.mp_beta / 3.0;
   for (int k = 0; k < 6; ++k) d.d[k] = s.d[k];
   d.exact_decisions = (s.decisions == TENOM_DECIDE_FP64) ? 1 : 0;
+  d.ct_const_f = (float)s.ct_const;
   d.default_d = 1;
   for (int k = 0; k < s.K - 2; ++k)
     if (s.d[k] != ((s.K == 6) ? kDopt6[k] : kDopt8[k])) d.default_d = 0;

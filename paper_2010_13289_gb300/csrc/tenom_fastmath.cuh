@@ -74,4 +74,18 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
   return fma(y, r, y);
 }
 
+/* FP64 -> FP32 rounded toward zero, on the integer pipe (the F2F conversion instruction runs
+   on the FP64 pipe, the scarce unit here).  |x - f| < 2^-23 |x| in the FP32 normal range;
+   magnitudes below it become a signed zero, above it (and NaN) infinity. */
+__device__ __forceinline__ float f32_rz(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+  return __uint_as_float(sign | ((unsigned)e << 23) | m);
+}
+
 }  // namespace tenom

@@ -36,7 +36,7 @@ struct SchemeDev {
   int weights;
   int default_d;         /* d_k are the maximal-order weights (central formula applies) */
   int exact_decisions;   /* 1: decide the cutoff in FP64 only (no certified FP32 filter) */
-  int pad_;
+  float ct_const_f;       /* ct_const rounded to FP32 (certified filter) */
   double ct_const;
   double mp_alpha;
   double mp_beta_third;  /* mp_beta / 3 */
@@ -223,8 +223,10 @@ __device__ __forceinline__ double adaptive_ct(const double* D, int* e) {
    TENO8A).  FP32 runs on the SM's wide FP32 pipe; GB300's FP64 pipe is the bottleneck.
    Every FP32 indicator is evaluated together with its absolute-value form (same form,
    |coefficients|, on |D|), which bounds its rounding error: for a form with n differences,
-   |beta_fp32 - beta| <= (3n + 7) u beta_abs with u = 2^-24 (dot-product error analysis,
-   including the conversion of D to FP32); C = 64 u doubles that.  The bounds are carried
+   |beta_fp32 - beta| <= (3n + 9) u beta_abs with u = 2^-24 (dot-product error analysis,
+   including the conversion of D to FP32 by truncation, relative error below 2u; a
+   difference below the FP32 normal range becomes 0, an absolute error far below the
+   bound); C = 64 u covers n <= 7 with room.  The bounds are carried
    through tau, gamma_k = (1 + tau/beta_k)^6 (scaled by the largest gamma to stay in range)
    and the comparison gamma_k < C_T sum gamma.  A decision is returned only when the whole
    interval lies on one side; otherwise (and for out-of-range data or an indicator that may
@@ -242,7 +244,7 @@ __device__ __forceinline__ bool cutoff_filter(const double (&D)[K - 1], const Sc
   float dmax = 0.f;
 #pragma unroll
   for (int t = 0; t < K - 1; ++t) {
-    d[t] = __double2float_rn(D[t]);
+    d[t] = f32_rz(D[t]);
     a[t] = fabsf(d[t]);
     dmax = fmaxf(dmax, a[t]);
   }
@@ -300,7 +302,7 @@ __device__ __forceinline__ bool cutoff_filter(const double (&D)[K - 1], const Sc
   }
   Sl *= 1.f - 8.f * u;
   Sh *= 1.f + 8.f * u;
-  double CT = S.ct_const;
+  float CTf = S.ct_const_f;
   ex = 7;
   if (S.ct_mode == CT_ADAPTIVE) {
     const float xi = 1e-3f, Cr = 0.23f, a1 = 10.5f, a2 = 3.5f;
@@ -320,9 +322,9 @@ __device__ __forceinline__ bool cutoff_filter(const double (&D)[K - 1], const Sc
     int x = (int)floorf(beta);
     x = x < 7 ? 7 : (x > 10 ? 10 : x);
     ex = x;
-    CT = x == 7 ? 1e-7 : (x == 8 ? 1e-8 : (x == 9 ? 1e-9 : 1e-10));
+    CTf = x == 7 ? 1e-7f : (x == 8 ? 1e-8f : (x == 9 ? 1e-9f : 1e-10f));
   }
-  const float CTf = __double2float_rn(CT);
+  if (!(CTf >= 1e-30f)) return false;  /* C_T below the FP32 normal range: decide in FP64 */
   const float thl = CTf * (1.f - 2.f * u) * Sl * (1.f - u), thh = CTf * (1.f + 2.f * u) * Sh * (1.f + u);
   unsigned bt = 0;
 #pragma unroll
