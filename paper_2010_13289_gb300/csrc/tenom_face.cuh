@@ -43,7 +43,9 @@ struct PointLayout {
 };
 
 constexpr int FX_FACES = 128;  /* faces per CTA, x sweeps */
-constexpr int FT_FACES = 8;    /* faces per CTA along the axis, y/z sweeps (x 32 lanes) */
+/* faces per CTA along the axis, y/z sweeps (x 32 lanes): 4 for K = 6 (128-thread CTAs
+   leave the compiler room for ~160 registers), 8 for K = 8 (halo K - 1 = 7 rows) */
+__host__ __device__ constexpr int ft_faces(int K) { return K == 6 ? 4 : 8; }
 constexpr int QSLOTS = 64;     /* reconstruction queue items per warp: two sides x 32 lanes */
 
 template <int NV, int K, int AXIS>
@@ -51,7 +53,7 @@ struct FaceTile {
   static constexpr int H = K / 2;
   static constexpr int NC = PointLayout<NV>::NC;
   static constexpr int LANES = (AXIS == 0) ? 1 : 32;
-  static constexpr int FACES = (AXIS == 0) ? FX_FACES : FT_FACES;
+  static constexpr int FACES = (AXIS == 0) ? FX_FACES : ft_faces(K);
   static constexpr int ROWS = FACES + K - 1;     /* points along the axis */
   static constexpr int NP = ROWS * LANES;        /* points per tile */
   static constexpr int THREADS = FACES * LANES;

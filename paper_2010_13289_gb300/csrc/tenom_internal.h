@@ -17,15 +17,15 @@ cudaError_t launch_face_rec_nv5(const FaceArgs& a, int axis, int K, int lim, cud
 /* Launch geometry of a face sweep (kept in one place for the tests of the host logic). */
 inline void face_grid(int nv, int axis, const int* n, int K, dim3* grid, dim3* block) {
   (void)nv;
-  (void)K;
   if (axis == 0) {
     *block = dim3(FX_FACES);
     *grid = dim3((unsigned)(n[1] * n[2]), (unsigned)((n[0] + 1 + FX_FACES - 1) / FX_FACES));
   } else {
     const int na = n[axis];
     const int other = (axis == 1) ? n[2] : n[1];
-    *block = dim3(32 * FT_FACES);
-    *grid = dim3((unsigned)((n[0] + 31) / 32), (unsigned)((na + 1 + FT_FACES - 1) / FT_FACES), (unsigned)other);
+    const int ft = ft_faces(K);
+    *block = dim3(32 * ft);
+    *grid = dim3((unsigned)((n[0] + 31) / 32), (unsigned)((na + 1 + ft - 1) / ft), (unsigned)other);
   }
 }
 
