@@ -320,12 +320,13 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
     __syncwarp(am);  /* read back before the queue is refilled */
   };
 
-  /* Deferred-queue path: the acoustic pair and the entropy field share the vectors
+  /* Forward without recording: the acoustic pair and the entropy field share the vectors
      a = (b2, -b1 u, b1) and b = (u_n / c, -e_n / c, 0): l_{u-+c} = (a +- b)/2, l_0 = e_0 - a.
      Per stencil point A = a.U/2, B = b.U/2, AF = a.F/4, BF = b.F/4 once, then
      W_{u-+c} = A +- B, G_{u-+c}/2 = AF +- BF, W_0 = rho - 2A, G_0/2 = F_rho/2 - 2AF. */
-  double pA[DQ ? K : 1], pB[DQ ? K : 1], pAF[DQ ? K : 1], pBF[DQ ? K : 1];
-  if constexpr (DQ) {
+  constexpr bool SH = !REC && K == 6;  /* K = 8: the arrays cost more occupancy than they save */
+  double pA[SH ? K : 1], pB[SH ? K : 1], pAF[SH ? K : 1], pBF[SH ? K : 1];
+  if constexpr (SH) {
     double ah[NV], aq[NV];
     ah[0] = 0.5 * b2;
 #pragma unroll
@@ -379,14 +380,14 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
        g+- = (G +- alpha W)/2, evaluated as fma(+-alpha/2, W, G/2) */
     const double ha = 0.5 * ((s == 0) ? a_m : (s == NV - 1 ? a_p : a_0));
     double gp[K], gm[K], Wr[REC ? K : 1];
-    if (DQ && acoustic) {
+    if (SH && acoustic) {
 #pragma unroll
       for (int q = 0; q < K; ++q) {
         const double w = fma(sg, pB[q], pA[q]), hg = fma(sg, pBF[q], pAF[q]);
         gp[q] = fma(ha, w, hg);
         gm[q] = fma(-ha, w, hg);
       }
-    } else if (DQ && s == 1) {
+    } else if (SH && s == 1) {
 #pragma unroll
       for (int q = 0; q < K; ++q) {
         const double w = fma(-2.0, pA[q], P(L::cU, q)), hg = fma(-2.0, pAF[q], 0.5 * P(L::cF, q));
