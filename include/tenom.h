@@ -71,7 +71,9 @@ typedef struct tenom_grid {
  * maximal-order d_k (Section 3.3 leaves the choice open). */
 typedef struct tenom_scheme {
   int K;            /* 6 or 8 (Eq. rdistribution: candidates S_0..S_{K-3}) */
-  int limiter;      /* TENOM_LIM_* */
+  int limiter;      /* TENOM_LIM_*: MP and TVD5 everywhere; VA (Van Albada, kappa = 1/3) for the
+                       forward calls only -- the adjoint calls return TENOM_E_UNSUPPORTED and
+                       tenom_batch_create rejects it */
   int ct_mode;      /* TENOM_CT_* */
   double ct_const;  /* C_T when ct_mode == TENOM_CT_CONST */
   double mp_alpha;

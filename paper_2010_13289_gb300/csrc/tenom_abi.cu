@@ -299,9 +299,9 @@ static tenom_status validate(const tenom_grid* g, const tenom_scheme* s, std::st
   if (nc > (1ll << 31)) { *msg = "grid too large"; return TENOM_E_INVALID; }
   if (g->dim > 1 && (long long)g->n[1] * g->n[2] > 2147483647ll) { *msg = "too many rows"; return TENOM_E_INVALID; }
   if (s->K != 6 && s->K != 8) { *msg = "K must be 6 or 8"; return TENOM_E_INVALID; }
-  if (s->limiter != TENOM_LIM_MP && s->limiter != TENOM_LIM_TVD5) {
-    *msg = "limiter not built (MP and TVD5 are)";
-    return TENOM_E_UNSUPPORTED;
+  if (s->limiter != TENOM_LIM_MP && s->limiter != TENOM_LIM_TVD5 && s->limiter != TENOM_LIM_VA) {
+    *msg = "bad limiter";
+    return TENOM_E_INVALID;
   }
   if (s->ct_mode != TENOM_CT_CONST && s->ct_mode != TENOM_CT_ADAPTIVE) { *msg = "bad ct_mode"; return TENOM_E_INVALID; }
   if (s->mp_curv != TENOM_CURV_M4 && s->mp_curv != TENOM_CURV_MM) { *msg = "bad mp_curv"; return TENOM_E_INVALID; }
@@ -630,6 +630,15 @@ static size_t flags_offset(const tenom_ctx* c, int axis) {
   return b;
 }
 
+/* The frozen-branch adjoint covers the limiters whose filtered candidate is a selection
+   among linear forms (MP, TVD5); the Van Albada flux is a smooth nonlinear function of the
+   stencil and has no frozen linear form here. */
+static bool adjoint_unsupported(tenom_ctx* c, const char* what) {
+  if (c->s.limiter != TENOM_LIM_VA) return false;
+  fail(c, TENOM_E_UNSUPPORTED, std::string(what) + ": no adjoint for the Van Albada limiter");
+  return true;
+}
+
 /* doubles of the linearisation one stage records for one face: NV x (2K + 2) */
 static size_t lin_per_face(const tenom_ctx* c) { return (size_t)c->nv * (2 * c->s.K + 2); }
 
@@ -691,6 +700,7 @@ static cudaError_t lincomb(tenom_ctx* c, double* out, double c0, const double* x
 
 tenom_status tenom_rhs_vjp(tenom_ctx* c, const double* U, const double* w, double* Ubar) {
   if (!c) return TENOM_E_INVALID;
+  if (adjoint_unsupported(c, "rhs_vjp")) return TENOM_E_UNSUPPORTED;
   if (!aligned8(U) || !aligned8(w) || !aligned8(Ubar) || Ubar == U || Ubar == w)
     return fail(c, TENOM_E_INVALID, "rhs_vjp: bad pointers");
   cudaError_t e = adj_sweeps(c, U, nullptr, nullptr, w, Ubar);
@@ -699,6 +709,7 @@ tenom_status tenom_rhs_vjp(tenom_ctx* c, const double* U, const double* w, doubl
 
 tenom_status tenom_rhs_record(tenom_ctx* c, const double* U, double* dUdt, double* lin) {
   if (!c) return TENOM_E_INVALID;
+  if (adjoint_unsupported(c, "rhs_record")) return TENOM_E_UNSUPPORTED;
   if (!aligned8(U) || !aligned8(dUdt) || U == dUdt || !aligned8(lin))
     return fail(c, TENOM_E_INVALID, "rhs_record: bad pointers");
   cudaError_t e = cudaSuccess;
@@ -710,6 +721,7 @@ tenom_status tenom_rhs_record(tenom_ctx* c, const double* U, double* dUdt, doubl
 
 tenom_status tenom_rhs_vjp_lin(tenom_ctx* c, const double* U, const double* lin, const double* w, double* Ubar) {
   if (!c) return TENOM_E_INVALID;
+  if (adjoint_unsupported(c, "rhs_vjp_lin")) return TENOM_E_UNSUPPORTED;
   if (!aligned8(U) || !aligned8(lin) || !aligned8(w) || !aligned8(Ubar) || Ubar == U || Ubar == w)
     return fail(c, TENOM_E_INVALID, "rhs_vjp_lin: bad pointers");
   cudaError_t e = adj_sweeps(c, U, nullptr, lin, w, Ubar);
@@ -736,6 +748,7 @@ static cudaError_t rk3_record(tenom_ctx* c, double* U, double* U1, double* U2, u
 
 static tenom_status record_step(tenom_ctx* c, double* U, const double* dt_dev, double* tape_states, uint8_t* fl,
                                 double* lin, const char* what) {
+  if (adjoint_unsupported(c, what)) return TENOM_E_UNSUPPORTED;
   cudaError_t e = cudaSuccess;
   if (dt_dev != c->dt) e = cudaMemcpyAsync(c->dt, dt_dev, sizeof(double), cudaMemcpyDeviceToDevice, c->st);
   const long long n = c->nv * c->ncell;
@@ -762,6 +775,7 @@ tenom_status tenom_rk3_step_record_lin(tenom_ctx* c, double* U, const double* dt
 /* reverse of one recorded step; per stage the sweeps read flags (fl) or the linearisation (lin) */
 static tenom_status adjoint_step(tenom_ctx* c, const double* U_n, const double* tape_states, const uint8_t* fl,
                                  const double* lin, const double* dt_dev, const double* Ubar_np1, double* Ubar_n) {
+  if (adjoint_unsupported(c, "rk3_step_adjoint")) return TENOM_E_UNSUPPORTED;
   cudaError_t e = ensure_adj(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "rk3_step_adjoint");
   const long long n = c->nv * c->ncell;
@@ -809,6 +823,7 @@ tenom_status tenom_rk3_step_adjoint_lin(tenom_ctx* c, const double* U_n, const d
 tenom_status tenom_rk3_step_adjoint(tenom_ctx* c, const double* U_n, const double* dt_dev, const double* Ubar_np1,
                                     double* Ubar_n) {
   if (!c) return TENOM_E_INVALID;
+  if (adjoint_unsupported(c, "rk3_step_adjoint")) return TENOM_E_UNSUPPORTED;
   if (!aligned8(U_n) || !aligned8(dt_dev)) return fail(c, TENOM_E_INVALID, "rk3_step_adjoint: bad pointers");
   cudaError_t e = ensure_adj(c);
   if (e != cudaSuccess) return cuda_fail(c, e, "rk3_step_adjoint");

@@ -34,9 +34,13 @@ static cudaError_t launch_face_axis(const FaceArgs& a, int K, int lim, cudaStrea
   if (K == 6) {
     if (lim == LIM_MP) return launch_face_one<NV, 6, LIM_MP, AXIS, REC>(a, st);
     if (lim == LIM_TVD5) return launch_face_one<NV, 6, LIM_TVD5, AXIS, REC>(a, st);
+    if constexpr (!REC)  /* Van Albada: forward only (no frozen linear form to record) */
+      if (lim == LIM_VA) return launch_face_one<NV, 6, LIM_VA, AXIS, false>(a, st);
   } else if (K == 8) {
     if (lim == LIM_MP) return launch_face_one<NV, 8, LIM_MP, AXIS, REC>(a, st);
     if (lim == LIM_TVD5) return launch_face_one<NV, 8, LIM_TVD5, AXIS, REC>(a, st);
+    if constexpr (!REC)
+      if (lim == LIM_VA) return launch_face_one<NV, 8, LIM_VA, AXIS, false>(a, st);
   }
   return cudaErrorNotSupported;
 }

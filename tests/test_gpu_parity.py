@@ -80,6 +80,69 @@ def test_face_flux_parity(T, orc, shape, bc, K, lim, jumps):
     assert S.status() == 0
 
 
+def face_parity_checks(T, orc, S, g, so, Uo, Ug, shape):
+    for a in range(len(shape)):
+        Fg, flg = S.face_dump(Ug, a)
+        Fo, flo, cut, noise, bad, scale = orc.faces(g, so, Uo, a, with_scale=True)
+        assert bad == 0
+        st = compare_faces(Fg.cpu().numpy(), flg.cpu().numpy(), Fo, flo, cut, noise, scale,
+                           label="%s axis %d" % (shape, a))
+        assert st["near_cutoff_faces"] <= max(2, 0.01 * st["faces"]), st
+    assert S.status() == 0
+
+
+# Scheme options beyond the two benchmarked ones: the Van Albada limiter (TENO-M-VA,
+# Section 3.2.3), the MP variants with the 2-argument minmod curvature and beta = 2 / 1
+# (Sections 3.2.2, 4), the classical renormalised TENO weights (Eq. weight_renormalize),
+# non-maximal-order d_k (no central-formula shortcut), the constant and adaptive C_T on the
+# other stencil width, a larger MP alpha.
+VARIANTS = [
+    ((70, 45), (0, 0), 6, 2, {}),
+    ((70, 45), (1, 0), 8, 2, {}),
+    ((20, 13, 11), (0, 1, 0), 8, 2, {}),
+    ((300,), (1,), 6, 2, {}),
+    ((70, 45), (0, 0), 6, 0, {"mp_curv": 1, "mp_beta": 2.0}),
+    ((70, 45), (0, 1), 8, 0, {"mp_curv": 1, "mp_beta": 1.0}),
+    ((70, 45), (0, 0), 6, 0, {"mp_alpha": 2.0}),
+    ((70, 45), (0, 0), 6, 0, {"weights": 1}),
+    ((70, 45), (1, 1), 8, 0, {"weights": 1}),
+    ((70, 45), (0, 0), 6, 0, {"d": (0.4, 0.3, 0.1, 0.2)}),
+    ((70, 45), (0, 0), 8, 1, {"d": (0.3, 0.25, 0.1, 0.2, 0.05, 0.1)}),
+    ((70, 45), (0, 0), 8, 0, {"ct_mode": 0, "ct_const": 1e-6}),
+    ((70, 45), (0, 0), 6, 1, {"ct_mode": 1}),
+]
+
+
+@pytest.mark.parametrize("shape,bc,K,lim,kw", VARIANTS)
+def test_face_flux_parity_scheme_variants(T, orc, shape, bc, K, lim, kw):
+    prim = PB.random_state(tuple(reversed(shape)), seed=sum(shape) + 7 * K + lim, jumps=True)
+    S, g, so, Uo, Ug = setup(T, orc, shape, bc, K, lim, prim, **kw)
+    face_parity_checks(T, orc, S, g, so, Uo, Ug, shape)
+    S.close()
+
+
+def test_van_albada_steps_match_and_adjoint_is_refused(T, orc):
+    """TENO-M-VA through SSP-RK3 steps agrees with the oracle; its adjoint is reported as
+    not supported (the Van Albada flux is not a selection among linear forms)."""
+    shape = (48, 40)
+    prim = PB.random_state((40, 48), seed=21, jumps=True)
+    S, g, so, Uo, Ug = setup(T, orc, shape, (0, 0), 6, T.LIM_VA, prim)
+    dto = orc.max_dt(g, Uo, 0.4)
+    dt = torch.tensor([dto], dtype=torch.float64, device="cuda")
+    U1o, _ = orc.rk3_step(g, so, Uo, dto)
+    U1g = S.rk3_step(Ug.clone(), dt).cpu().numpy()
+    err = np.abs(U1g - U1o) / np.maximum(np.abs(U1o), 1e-3 * np.abs(U1o).max(axis=(1, 2), keepdims=True))
+    assert float(np.mean(err > 1e-12)) < 0.01 and np.median(err) < 1e-15
+    with pytest.raises(T.TenomError) as ei:
+        S.rhs_vjp(Ug, Ug.clone())
+    assert ei.value.status == T.TENOM_E_UNSUPPORTED
+    with pytest.raises(T.TenomError):
+        S.rk3_step_adjoint(Ug, dt, Ug.clone())
+    with pytest.raises(T.TenomError):
+        S.rk3_step_record(Ug.clone(), dt, S.new_tape(linear=True))
+    S.close()
+
+
 @pytest.mark.parametrize("K,lim", [(6, 0), (8, 1), (8, 0)])
 def test_rk3_step_and_max_dt_parity(T, orc, K, lim):
     shape = (48, 40)
