@@ -534,6 +534,58 @@ def _linear_tape(S, steps, tape):
     return _use_linear(S, steps, tape)
 
 
+COST_VARIANTS = [
+    # (label, K, limiter, weights): the paper's cost comparison (Section 4) is TENO-M with
+    # each limiter against the classical TENO with renormalised weights on the same stencil
+    ("TENO6", 6, 0, 1), ("TENO6-M-MP", 6, 0, 0), ("TENO6-M-TVD5", 6, 1, 0), ("TENO6-M-VA", 6, 2, 0),
+    ("TENO8A", 8, 0, 1), ("TENO8A-M-MP", 8, 0, 0), ("TENO8A-M-TVD5", 8, 1, 0), ("TENO8A-M-VA", 8, 2, 0),
+]
+
+
+def run_cost_ratios(args):
+    """Time per SSP-RK3 step of TENO-M with MP / TVD5 / VA relative to the classical TENO
+    (renormalised weights, no limiter) on the 2D 2048^2 broadband field, K = 6 and K = 8.
+    The paper quotes MP at about 1.09-1.12x and TVD-type limiters at about 0.99x TENO8A
+    (CPU, its own hardware); these are the GPU kernels' ratios."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2010_13289_gb300 import tenom as T
+    shape = (2048, 2048)
+    prim, dx = make_prim("broadband_2d_2048_teno6_mp", args.seed)
+    primd = torch.from_numpy(prim).cuda()
+    stream = torch.cuda.current_stream()
+    times = {}
+    clocks = ClockSampler(0)
+    clocks.start()
+    for label, K, lim, w in COST_VARIANTS:
+        S = T.Solver(shape, dx, (T.BC_PERIODIC,) * 2, T.make_scheme(K, limiter=lim, weights=w))
+        U = S.init_state(primd)
+        S.advance(U, args.warmup)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        S.advance(U, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times[label] = e0.elapsed_time(e1) / args.steps
+        S.close()
+    clk = clocks.stop()
+    ncell = float(np.prod(shape))
+    out = {"metric": "time per SSP-RK3 step relative to TENO (renormalised weights)", "unit": "ratio",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "higher_is_better": False,
+           "dtype": "f64", "data": "synthetic (seeded, shaped like the paper's workloads)",
+           "config": {"workload": "cost_ratios_2d_2048", "shape": list(shape)},
+           "ms_per_step": times,
+           "cell_updates_per_s": {k: ncell * 3 / (v * 1e-3) for k, v in times.items()},
+           "ratios": {k: times[k] / times[k.split("-")[0]] for k in times},
+           "paper": {"MP": "1.09-1.12 x TENO8A", "TVD": "0.99 x TENO8A"},
+           "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
 def run_adjoint(args):
     """Adjoint workload: 2D 512^2 broadband field with circular jumps, TENO6-MP, 200 SSP-RK3
     steps at a fixed dt, loss = integral of p over a seeded 64 x 64 window at the end;
@@ -636,7 +688,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT,
-                    choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(ADJOINT_WORKLOADS))
+                    choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(ADJOINT_WORKLOADS) + ["cost_ratios_2d_2048"])
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--ref-seconds", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -655,6 +707,8 @@ def main():
         run_batch(args)
     elif args.workload in ADJOINT_WORKLOADS:
         run_adjoint(args)
+    elif args.workload == "cost_ratios_2d_2048":
+        run_cost_ratios(args)
     else:
         run_ours(args)
 
