@@ -368,7 +368,7 @@ def run_ours(args):
             "frac_fp64_issue": fpi * faces_per_launch / (face_ms * 1e-3) / (304 * mhz * 1e6) if face_ms > 0 else None,
             "note": "FP64 instructions the kernel executes (ncu, %s) at the live launch time over the "
                     "FP64 pipe's 304 lanes per clock" % fig["file"]}
-    launches_per_step = 3 + 3 * (len(shape) + 1)
+    launches_per_step = 3 + 3 * (len(shape) + 2)  # per stage: primitives, one sweep per axis, update; dt
 
     out = {"metric": "cell-updates/s per RK stage (FP64)", "value": value, "unit": "cell-updates/s",
            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,

@@ -162,6 +162,26 @@ __global__ void finalize_dt_kernel(unsigned long long* smax, double cfl, double*
 __global__ void advance_time_kernel(double* t, const double* dt) { *t = *t + *dt; }
 
 /* Compare the Newton-Raphson reciprocal / rsqrt with CUDA's correctly rounded 1.0/x, sqrt. */
+/* per-cell primitives for the face sweeps of one stage: P = [velocity (NV-2), p, H, c, sqrt rho] */
+template <int NV>
+__global__ void prim_kernel(const double* __restrict__ U, long long ncell, double gamma, double* __restrict__ P,
+                            int* status) {
+  int st = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncell; i += (long long)gridDim.x * blockDim.x) {
+    double u[NV], vel[NV - 2], pr, Hh, c, sr;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) u[q] = U[q * ncell + i];
+    point_prims<NV>(u, gamma, vel, pr, Hh, c, sr, st);
+#pragma unroll
+    for (int d = 0; d < NV - 2; ++d) P[d * ncell + i] = vel[d];
+    P[(NV - 2) * ncell + i] = pr;
+    P[(NV - 1) * ncell + i] = Hh;
+    P[NV * ncell + i] = c;
+    P[(NV + 1) * ncell + i] = sr;
+  }
+  if (st) atomicOr(status, st);
+}
+
 __global__ void fastmath_check_kernel(const double* x, double* out, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double v = x[i];
@@ -218,6 +238,7 @@ struct tenom_ctx {
   long long nface[3];
   double* W1;          /* stage buffer */
   double* face[3];     /* face buffers */
+  double* P;           /* per-cell primitives of the stage being evaluated ([nvar + 2][ncell]) */
   double* dt;          /* device dt */
   double* tbuf;        /* device scratch time */
   double* Uhost;       /* device state for tenom_advance_host (allocated on first use) */
@@ -351,6 +372,7 @@ tenom_status tenom_create(tenom_ctx** out, const tenom_grid* grid, const tenom_s
   c->face_launches = 0;
   cudaError_t e = cudaMalloc(&c->W1, sizeof(double) * c->nv * c->ncell);
   for (int a = 0; a < grid->dim && e == cudaSuccess; ++a) e = cudaMalloc(&c->face[a], sizeof(double) * c->nv * c->nface[a]);
+  if (e == cudaSuccess) e = cudaMalloc(&c->P, sizeof(double) * (c->nv + 2) * c->ncell);
   if (e == cudaSuccess) e = cudaMalloc(&c->dt, sizeof(double) * 2);
   if (e == cudaSuccess) e = cudaMalloc(&c->smax, sizeof(unsigned long long) + sizeof(int) * 2);
   if (e == cudaSuccess) {
@@ -373,6 +395,7 @@ tenom_status tenom_destroy(tenom_ctx* c) {
   cudaStreamSynchronize(c->st);
   cudaFree(c->W1);
   for (int a = 0; a < 3; ++a) cudaFree(c->face[a]);
+  cudaFree(c->P);
   cudaFree(c->dt);
   cudaFree(c->smax);
   cudaFree(c->Uhost);
@@ -423,9 +446,10 @@ static FaceArgs face_args(tenom_ctx* c, const double* U, int axis, double* F, ui
 }
 
 static cudaError_t launch_faces(tenom_ctx* c, const double* U, int axis, double* F, uint8_t* flags,
-                                double* lin = nullptr) {
+                                double* lin = nullptr, const double* P = nullptr) {
   FaceArgs a = face_args(c, U, axis, F, flags);
   a.lin = lin;
+  a.P = P;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->timing) {
     while (c->ev.size() < c->ev_used + 2) {
@@ -478,12 +502,20 @@ static cudaError_t launch_stage(tenom_ctx* c, const double* U0, const double* Us
   return cudaGetLastError();
 }
 
+/* the cell primitives of U into c->P (read by the face sweeps of this stage) */
+static cudaError_t launch_prims(tenom_ctx* c, const double* U) {
+  const unsigned nb = ew_blocks(c->ncell);
+  if (c->nv == 3) prim_kernel<3><<<nb, 256, 0, c->st>>>(U, c->ncell, c->g.gamma, c->P, c->status);
+  else if (c->nv == 4) prim_kernel<4><<<nb, 256, 0, c->st>>>(U, c->ncell, c->g.gamma, c->P, c->status);
+  else prim_kernel<5><<<nb, 256, 0, c->st>>>(U, c->ncell, c->g.gamma, c->P, c->status);
+  return cudaGetLastError();
+}
+
+/* face fluxes of every axis at U: the cell primitives once, then one sweep per axis */
 static cudaError_t eval_faces(tenom_ctx* c, const double* U) {
-  for (int a = 0; a < c->g.dim; ++a) {
-    cudaError_t e = launch_faces(c, U, a, c->face[a], nullptr);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  cudaError_t e = launch_prims(c, U);
+  for (int a = 0; a < c->g.dim && e == cudaSuccess; ++a) e = launch_faces(c, U, a, c->face[a], nullptr, nullptr, c->P);
+  return e;
 }
 
 tenom_status tenom_rhs(tenom_ctx* c, const double* U, double* dUdt) {
@@ -659,12 +691,14 @@ static size_t lin_offset(const tenom_ctx* c, int axis) {
 static cudaError_t adj_sweeps(tenom_ctx* c, const double* U, const uint8_t* flags_stage, const double* lin_stage,
                               const double* w, double* Z) {
   cudaError_t e = cudaMemsetAsync(Z, 0, sizeof(double) * c->nv * c->ncell, c->st);
+  if (e == cudaSuccess) e = launch_prims(c, U);
   for (int a = 0; a < c->g.dim && e == cudaSuccess; ++a) {
     AdjArgs A;
     memset(&A, 0, sizeof(A));
     A.U = U;
     A.flags = flags_stage ? flags_stage + flags_offset(c, a) : nullptr;
     A.lin = lin_stage ? lin_stage + lin_offset(c, a) : nullptr;
+    A.P = c->P;
     A.w = w;
     A.Z = Z;
     A.status = c->status;
@@ -712,9 +746,9 @@ tenom_status tenom_rhs_record(tenom_ctx* c, const double* U, double* dUdt, doubl
   if (adjoint_unsupported(c, "rhs_record")) return TENOM_E_UNSUPPORTED;
   if (!aligned8(U) || !aligned8(dUdt) || U == dUdt || !aligned8(lin))
     return fail(c, TENOM_E_INVALID, "rhs_record: bad pointers");
-  cudaError_t e = cudaSuccess;
+  cudaError_t e = launch_prims(c, U);
   for (int a = 0; a < c->g.dim && e == cudaSuccess; ++a)
-    e = launch_faces(c, U, a, c->face[a], nullptr, lin + lin_offset(c, a));
+    e = launch_faces(c, U, a, c->face[a], nullptr, lin + lin_offset(c, a), c->P);
   if (e == cudaSuccess) e = launch_stage(c, nullptr, U, dUdt, 0, 0.0, 0.0);
   return e == cudaSuccess ? TENOM_OK : cuda_fail(c, e, "rhs_record");
 }
@@ -735,9 +769,10 @@ static cudaError_t rk3_record(tenom_ctx* c, double* U, double* U1, double* U2, u
   const double* src[3] = {U, U1, U2};
   cudaError_t e = cudaSuccess;
   for (int st = 0; st < 3 && e == cudaSuccess; ++st) {
+    e = launch_prims(c, src[st]);
     for (int a = 0; a < c->g.dim && e == cudaSuccess; ++a)
       e = launch_faces(c, src[st], a, c->face[a], fl ? fl + st * fb + flags_offset(c, a) : nullptr,
-                       lin ? lin + st * lb + lin_offset(c, a) : nullptr);
+                       lin ? lin + st * lb + lin_offset(c, a) : nullptr, c->P);
     if (e != cudaSuccess) break;
     if (st == 0) e = launch_stage(c, nullptr, U, U1, 1, 0.0, 1.0);
     else if (st == 1) e = launch_stage(c, U, U1, U2, 2, 0.75, 0.25);

@@ -20,6 +20,7 @@ struct AdjArgs {
   const double* U;       /* state the operator was applied to [NV][ncell] */
   const uint8_t* flags;  /* forward flags of this axis [nface][NV][2], or null */
   const double* lin;     /* recorded linearisation of this axis [NV][2K+2][nface] (adj_lin_kernel) */
+  const double* P;       /* cell primitives of U [NV + 2][ncell] (velocity, p, H, c, sqrt rho), or null */
   const double* w;       /* cell adjoint [NV][ncell] */
   double* Z;             /* accumulated L'^T w [NV][ncell] */
   int* status;
@@ -92,7 +93,16 @@ __device__ __forceinline__ void adj_stage(const AdjArgs& A, const AdjTileMap<NV,
     double u[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) u[q] = __ldg(A.U + q * A.ncell + cell);
-    stage_point<NV, AXIS>(u, A.gamma, sm, T::NP, p, st);
+    if (A.P) {
+      double vel[NV - 2];
+#pragma unroll
+      for (int d = 0; d < NV - 2; ++d) vel[d] = __ldg(A.P + d * A.ncell + cell);
+      stage_point_from<NV, AXIS>(u, vel, __ldg(A.P + (NV - 2) * A.ncell + cell), __ldg(A.P + (NV - 1) * A.ncell + cell),
+                                 __ldg(A.P + NV * A.ncell + cell), __ldg(A.P + (NV + 1) * A.ncell + cell), sm, T::NP,
+                                 p);
+    } else {
+      stage_point<NV, AXIS>(u, A.gamma, sm, T::NP, p, st);
+    }
     const double c = sm[PointLayout<NV>::cC * T::NP + p], sr = sm[PointLayout<NV>::cS * T::NP + p];
     rec[p] = rcp_nr(u[0]);
     rec[T::NP + p] = rcp_nr(2.0 * c * u[0]);

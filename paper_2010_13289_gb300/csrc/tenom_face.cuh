@@ -24,6 +24,7 @@ struct FaceArgs {
   const double* U;    /* [NV][ncell] */
   double* Fhat;       /* [NV][nface] */
   uint8_t* flags;     /* [nface][NV][2] or null */
+  const double* P;    /* point primitives [NV + 2][ncell] (velocity, p, H, c, sqrt rho), or null */
   double* lin;        /* linearisation [NV][2K+2][nface] (record kernels only) */
   int* status;        /* sticky status word */
   int n[3];
@@ -71,25 +72,36 @@ __device__ __forceinline__ int bc_wrap(int j, int n, int bc) {
   return j < 0 ? 0 : (j >= n ? n - 1 : j);
 }
 
-/* Point quantities of the Euler equations for sweep axis AXIS (computed once per point):
-   U, the physical flux F_AXIS(U), velocity, H, c, sqrt(rho), |u_a - c|, |u_a + c|. */
-template <int NV, int AXIS>
-__device__ __forceinline__ void stage_point(const double (&u)[NV], double gamma, double* sm, int NP, int p, int& st) {
-  using L = PointLayout<NV>;
+/* Primitive quantities of one point: velocity, pressure p = (gamma - 1)(E - rho|u|^2/2),
+   total enthalpy H = (E + p)/rho, sound speed c = sqrt(gamma p / rho), sqrt(rho). */
+template <int NV>
+__device__ __forceinline__ void point_prims(const double (&u)[NV], double gamma, double (&vel)[NV - 2], double& pr,
+                                            double& Hh, double& c, double& sr, int& st) {
   constexpr int D = NV - 2;
   const double rho = u[0];
   const double rinv = rcp_nr(rho);
-  double vel[D], ke = 0.0;
+  double ke = 0.0;
 #pragma unroll
   for (int d = 0; d < D; ++d) {
     vel[d] = u[1 + d] * rinv;
     ke += u[1 + d] * vel[d];
   }
-  const double pr = (gamma - 1.0) * (u[NV - 1] - 0.5 * ke);
-  const double c = sqrt(gamma * pr * rinv);
-  const double Hh = (u[NV - 1] + pr) * rinv;
+  pr = (gamma - 1.0) * (u[NV - 1] - 0.5 * ke);
+  c = sqrt(gamma * pr * rinv);
+  Hh = (u[NV - 1] + pr) * rinv;
+  sr = sqrt(rho);
   if (!ipos(rho)) st |= ST_RHO;
   if (!ipos(pr)) st |= ST_P;
+}
+
+/* Point quantities of the Euler equations for sweep axis AXIS, written to the tile from U
+   and its primitives: U, the physical flux F_AXIS(U), velocity, H, c, sqrt(rho),
+   |u_a - c|, |u_a + c|. */
+template <int NV, int AXIS>
+__device__ __forceinline__ void stage_point_from(const double (&u)[NV], const double (&vel)[NV - 2], double pr,
+                                                 double Hh, double c, double sr, double* sm, int NP, int p) {
+  using L = PointLayout<NV>;
+  constexpr int D = NV - 2;
   const double un = vel[AXIS];
 #pragma unroll
   for (int q = 0; q < NV; ++q) sm[(L::cU + q) * NP + p] = u[q];
@@ -101,9 +113,17 @@ __device__ __forceinline__ void stage_point(const double (&u)[NV], double gamma,
   for (int d = 0; d < D; ++d) sm[(L::cV + d) * NP + p] = vel[d];
   sm[L::cH * NP + p] = Hh;
   sm[L::cC * NP + p] = c;
-  sm[L::cS * NP + p] = sqrt(rho);
+  sm[L::cS * NP + p] = sr;
   sm[L::cLm * NP + p] = iabs(un - c);
   sm[L::cLp * NP + p] = iabs(un + c);
+}
+
+/* Point quantities computed here (once per point of the tile). */
+template <int NV, int AXIS>
+__device__ __forceinline__ void stage_point(const double (&u)[NV], double gamma, double* sm, int NP, int p, int& st) {
+  double vel[NV - 2], pr, Hh, c, sr;
+  point_prims<NV>(u, gamma, vel, pr, Hh, c, sr, st);
+  stage_point_from<NV, AXIS>(u, vel, pr, Hh, c, sr, sm, NP, p);
 }
 
 /* Warp work queue for the two reconstructions (f+, f-) of one characteristic field.
@@ -537,7 +557,16 @@ face_kernel(const FaceArgs A) {
     double u[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) u[q] = __ldg(A.U + q * A.ncell + cell);
-    stage_point<NV, AXIS>(u, A.gamma, sm, T::NP, p, st);
+    if (A.P) {  /* primitives computed once per cell per stage (prim_kernel) */
+      double vel[NV - 2];
+#pragma unroll
+      for (int d = 0; d < NV - 2; ++d) vel[d] = __ldg(A.P + d * A.ncell + cell);
+      stage_point_from<NV, AXIS>(u, vel, __ldg(A.P + (NV - 2) * A.ncell + cell), __ldg(A.P + (NV - 1) * A.ncell + cell),
+                                 __ldg(A.P + NV * A.ncell + cell), __ldg(A.P + (NV + 1) * A.ncell + cell), sm, T::NP,
+                                 p);
+    } else {
+      stage_point<NV, AXIS>(u, A.gamma, sm, T::NP, p, st);
+    }
   }
   __syncthreads();
 
