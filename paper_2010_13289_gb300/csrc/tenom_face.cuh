@@ -344,7 +344,7 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
      a = (b2, -b1 u, b1) and b = (u_n / c, -e_n / c, 0): l_{u-+c} = (a +- b)/2, l_0 = e_0 - a.
      Per stencil point A = a.U/2, B = b.U/2, AF = a.F/4, BF = b.F/4 once, then
      W_{u-+c} = A +- B, G_{u-+c}/2 = AF +- BF, W_0 = rho - 2A, G_0/2 = F_rho/2 - 2AF. */
-  constexpr bool SH = !REC && K == 6;  /* K = 8: the arrays cost more occupancy than they save */
+  constexpr bool SH = K == 6;  /* K = 8: the arrays cost more occupancy than they save */
   double pA[SH ? K : 1], pB[SH ? K : 1], pAF[SH ? K : 1], pBF[SH ? K : 1];
   if constexpr (SH) {
     double ah[NV], aq[NV];
@@ -406,6 +406,7 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
         const double w = fma(sg, pB[q], pA[q]), hg = fma(sg, pBF[q], pAF[q]);
         gp[q] = fma(ha, w, hg);
         gm[q] = fma(-ha, w, hg);
+        if constexpr (REC) Wr[q] = w;
       }
     } else if (SH && s == 1) {
 #pragma unroll
@@ -413,6 +414,7 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
         const double w = fma(-2.0, pA[q], P(L::cU, q)), hg = fma(-2.0, pAF[q], 0.5 * P(L::cF, q));
         gp[q] = fma(ha, w, hg);
         gm[q] = fma(-ha, w, hg);
+        if constexpr (REC) Wr[q] = w;
       }
     } else if (acoustic || s == 1) {
 #pragma unroll
