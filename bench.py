@@ -243,7 +243,7 @@ def run_reference(args):
         v = statistics.median(rates)
         nprob, seed, nmin, nmax, K, lim = BATCH_WORKLOADS[name]
         out = {"impl": "reference", "metric": "cell-updates/s per RK stage (FP64)", "value": v,
-               "unit": "cell-updates/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+               "unit": "cell-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True, "scaling": "weak",
                "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded, shaped like the paper's workloads)",
                "config": {"workload": name, "problems": nprob, "K": K, "limiter": "MP" if lim == 0 else "TVD5"},
@@ -262,7 +262,7 @@ def run_reference(args):
     v = statistics.median(rates)
     gen, shape, K, lim = WORKLOADS[name]
     out = {"impl": "reference", "metric": "cell-updates/s per RK stage (FP64)", "value": v,
-           "unit": "cell-updates/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+           "unit": "cell-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * statistics.median(times), "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded, shaped like the paper's workloads)",
            "config": {"workload": name, "shape": list(shape), "K": K, "limiter": "MP" if lim == 0 else "TVD5"},
