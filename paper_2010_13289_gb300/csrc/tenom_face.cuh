@@ -44,9 +44,10 @@ struct PointLayout {
 };
 
 constexpr int FX_FACES = 128;  /* faces per CTA, x sweeps */
-/* faces per CTA along the axis, y/z sweeps (x 32 lanes): 4 for K = 6 (128-thread CTAs
-   leave the compiler room for ~160 registers), 8 for K = 8 (halo K - 1 = 7 rows) */
-__host__ __device__ constexpr int ft_faces(int K) { return K == 6 ? 4 : 8; }
+/* faces per CTA along the axis, y/z sweeps (x 32 lanes): 4, i.e. 128-thread CTAs that leave
+   the compiler room for ~168 registers (the halo rows cost little once the cell primitives
+   come from the per-stage kernel) */
+__host__ __device__ constexpr int ft_faces(int K) { return (void)K, 4; }
 constexpr int QSLOTS = 64;     /* reconstruction queue items per warp: two sides x 32 lanes */
 
 template <int NV, int K, int AXIS>
@@ -344,7 +345,7 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
      a = (b2, -b1 u, b1) and b = (u_n / c, -e_n / c, 0): l_{u-+c} = (a +- b)/2, l_0 = e_0 - a.
      Per stencil point A = a.U/2, B = b.U/2, AF = a.F/4, BF = b.F/4 once, then
      W_{u-+c} = A +- B, G_{u-+c}/2 = AF +- BF, W_0 = rho - 2A, G_0/2 = F_rho/2 - 2AF. */
-  constexpr bool SH = K == 6;  /* K = 8: the arrays cost more occupancy than they save */
+  constexpr bool SH = K == 6 || !REC;  /* recording with K = 8: the arrays cost more occupancy than they save */
   double pA[SH ? K : 1], pB[SH ? K : 1], pAF[SH ? K : 1], pBF[SH ? K : 1];
   if constexpr (SH) {
     double ah[NV], aq[NV];
