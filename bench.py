@@ -152,6 +152,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x, ws, device="cuda"):
+    """The largest x over the ranks of the job (x itself for one rank): every timing of the
+    replicas path is the slowest rank's."""
+    if ws <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_rate(units_per_rank, ws, seconds):
+    """Whole-job throughput of independent replicas: all ranks' units over the slowest time."""
+    return float(units_per_rank) * ws / seconds
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -315,14 +332,9 @@ def run_ours(args):
     barrier()
     face_ms, face_launches = S.kernel_timing(False)
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = t.item()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), ws)
     assert S.status() == 0, "non-physical state in the benchmark run"
-    updates = float(ncell) * 3 * args.steps * ws
-    value = updates / (ms * 1e-3)
+    value = job_rate(float(ncell) * 3 * args.steps, ws, ms * 1e-3)
 
     # end to end through the C ABI with host buffers: H2D of the state, one RK3 step, D2H
     host_in = torch.empty(S.state_shape, dtype=torch.float64, pin_memory=True)
@@ -335,12 +347,8 @@ def run_ours(args):
     for _ in range(e2e_steps):
         S.advance_host(host_in, host_out, nsteps=1)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if ws > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = t.item()
-    e2e = float(ncell) * 3 * e2e_steps * ws / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, ws)
+    e2e = job_rate(float(ncell) * 3 * e2e_steps, ws, e2e_s)
     state_bytes = 8 * S.nv * ncell
 
     # roofline of the dominant kernel (face flux): FP64-ALU bound
@@ -437,13 +445,9 @@ def run_batch(args):
     ev1.record(stream)
     barrier()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = t.item()
+    ms = max_over_ranks(ev0.elapsed_time(ev1), ws)
     assert B.status() == 0
-    value = float(B.total) * 3 * args.steps * ws / (ms * 1e-3)
+    value = job_rate(float(B.total) * 3 * args.steps, ws, ms * 1e-3)
 
     # the same problems advanced by separate plain launches (one context per problem)
     sep_steps = max(1, min(args.steps, 3))
