@@ -42,7 +42,7 @@ struct StageArgs {
   const double* dt;    /* device dt (null for rhs) */
   const double* t;     /* device time: steps at t >= t_end are skipped */
   int n[3];
-  double dx[3];
+  double rdx[3];       /* 1 / dx_a */
   long long ncell;
   long long nface[3];
   double cA, cB;       /* out = cA U0 + cB (Us + dt L); cA = 0, cB = 1 for stage 1 */
@@ -51,76 +51,88 @@ struct StageArgs {
 };
 
 /* Flux difference -sum_a (F_{a,i+1/2} - F_{a,i-1/2})/dx_a (Eq. approximateEq) fused with
-   the SSP-RK3 stage combine. */
+   the SSP-RK3 stage combine; 1/dx_a is formed once on the host (an FP64 division per cell
+   and axis would occupy the FP64 pipe longer than the kernel's memory traffic takes). */
 template <int NV>
 __global__ void stage_kernel(const StageArgs A) {
   constexpr int DIM = NV - 2;
   const long long nc = A.ncell;
-  double dt = 0.0;
-  if (A.mode != 0) {
-    dt = *A.dt;
-  }
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
-    const int x = (int)(c % A.n[0]);
-    const long long yz = c / A.n[0];
-    const int y = (int)(yz % A.n[1]);
-    const int z = (int)(yz / A.n[1]);
-    long long fl[3], fs[3];
-    fl[0] = x + (long long)(A.n[0] + 1) * yz;
-    fs[0] = 1;
-    if (DIM > 1) {
-      fl[1] = x + (long long)A.n[0] * (y + (long long)(A.n[1] + 1) * z);
-      fs[1] = A.n[0];
-    }
-    if (DIM > 2) {
-      fl[2] = c;
-      fs[2] = (long long)A.n[0] * A.n[1];
-    }
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
-      double r = 0.0;
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        const double* F = A.F[a] + v * A.nface[a];
-        r = r - (F[fl[a] + fs[a]] - F[fl[a]]) / A.dx[a];
+  const double dt = (A.mode != 0) ? *A.dt : 0.0;
+  /* one thread per cell: x from the block's column, y and z from the grid (strided when an
+     axis exceeds the grid's 65535 limit) */
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= A.n[0]) return;
+  for (int z = blockIdx.z; z < A.n[2]; z += gridDim.z) {
+    for (int y = blockIdx.y; y < A.n[1]; y += gridDim.y) {
+      const long long yz = y + (long long)A.n[1] * z;
+      const long long c = x + (long long)A.n[0] * yz;
+      long long fl[3], fs[3];
+      fl[0] = x + (long long)(A.n[0] + 1) * yz;
+      fs[0] = 1;
+      if (DIM > 1) {
+        fl[1] = x + (long long)A.n[0] * (y + (long long)(A.n[1] + 1) * z);
+        fs[1] = A.n[0];
       }
-      if (A.mode == 0) {
-        A.out[v * nc + c] = r;
-      } else if (dt == 0.0) {
-        /* a step past t_end: every stage state equals U^n, keep it bit for bit */
-        A.out[v * nc + c] = A.Us[v * nc + c];
-      } else {
-        const double us = A.Us[v * nc + c];
-        const double t1 = us + dt * r;
-        A.out[v * nc + c] = (A.mode == 1) ? t1 : A.cA * A.U0[v * nc + c] + A.cB * t1;
+      if (DIM > 2) {
+        fl[2] = c;
+        fs[2] = (long long)A.n[0] * A.n[1];
+      }
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        double r = 0.0;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+          const double* F = A.F[a] + v * A.nface[a];
+          r = r - (F[fl[a] + fs[a]] - F[fl[a]]) * A.rdx[a];
+        }
+        if (A.mode == 0) {
+          A.out[v * nc + c] = r;
+        } else if (dt == 0.0) {
+          /* a step past t_end: every stage state equals U^n, keep it bit for bit */
+          A.out[v * nc + c] = A.Us[v * nc + c];
+        } else {
+          const double us = A.Us[v * nc + c];
+          const double t1 = us + dt * r;
+          A.out[v * nc + c] = (A.mode == 1) ? t1 : A.cA * A.U0[v * nc + c] + A.cB * t1;
+        }
       }
     }
   }
 }
 
+static cudaError_t launch_stage_kernel(int nv, const StageArgs& a, cudaStream_t st) {
+  const dim3 grid((unsigned)((a.n[0] + 255) / 256), (unsigned)(a.n[1] < 65535 ? a.n[1] : 65535),
+                  (unsigned)(a.n[2] < 65535 ? a.n[2] : 65535));
+  if (nv == 3) stage_kernel<3><<<grid, 256, 0, st>>>(a);
+  else if (nv == 4) stage_kernel<4><<<grid, 256, 0, st>>>(a);
+  else stage_kernel<5><<<grid, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 /* max_i sum_a (|u_a| + c)/dx_a, reduced with atomicMax on the (positive) bit pattern. */
 template <int NV>
-__global__ void signal_speed_kernel(const double* __restrict__ U, long long nc, double gamma, double dx0,
-                                    double dx1, double dx2, unsigned long long* smax, int* status) {
+__global__ void signal_speed_kernel(const double* __restrict__ U, long long nc, double gamma, double rdx0,
+                                    double rdx1, double rdx2, unsigned long long* smax, int* status) {
   constexpr int DIM = NV - 2;
-  const double dx[3] = {dx0, dx1, dx2};
+  const double rdx[3] = {rdx0, rdx1, rdx2};
   double m = 0.0;
   int st = 0;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < nc; c += (long long)gridDim.x * blockDim.x) {
     const double rho = U[c];
+    const double rinv = rcp_nr(rho);
     double vel[DIM], ke = 0.0;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-      vel[d] = U[(1 + d) * nc + c] / rho;
+      vel[d] = U[(1 + d) * nc + c] * rinv;
       ke += U[(1 + d) * nc + c] * vel[d];
     }
     const double p = (gamma - 1.0) * (U[(NV - 1) * nc + c] - 0.5 * ke);
     if (!(rho > 0.0)) st |= ST_RHO;
     if (!(p > 0.0)) st |= ST_P;
-    const double cs = sqrt(gamma * p / rho);
+    const double cs = sqrt(gamma * p * rinv);
     double s = 0.0;
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) s += (fabs(vel[d]) + cs) / dx[d];
+    for (int d = 0; d < DIM; ++d) s += (fabs(vel[d]) + cs) * rdx[d];
     m = (s > m) ? s : m;
   }
   /* warp then block reduction */
@@ -484,7 +496,7 @@ static cudaError_t launch_stage(tenom_ctx* c, const double* U0, const double* Us
   for (int d = 0; d < 3; ++d) {
     a.F[d] = c->face[d];
     a.n[d] = c->g.n[d];
-    a.dx[d] = c->g.dx[d];
+    a.rdx[d] = 1.0 / c->g.dx[d];
     a.nface[d] = c->nface[d];
   }
   a.U0 = U0;
@@ -495,11 +507,7 @@ static cudaError_t launch_stage(tenom_ctx* c, const double* U0, const double* Us
   a.cA = cA;
   a.cB = cB;
   a.mode = mode;
-  unsigned nb = ew_blocks(c->ncell);
-  if (c->nv == 3) stage_kernel<3><<<nb, 256, 0, c->st>>>(a);
-  else if (c->nv == 4) stage_kernel<4><<<nb, 256, 0, c->st>>>(a);
-  else stage_kernel<5><<<nb, 256, 0, c->st>>>(a);
-  return cudaGetLastError();
+  return launch_stage_kernel(c->nv, a, c->st);
 }
 
 /* the cell primitives of U into c->P (read by the face sweeps of this stage) */
@@ -529,9 +537,10 @@ tenom_status tenom_rhs(tenom_ctx* c, const double* U, double* dUdt) {
 static cudaError_t launch_signal(tenom_ctx* c, const double* U) {
   unsigned nb = ew_blocks(c->ncell);
   const double* dx = c->g.dx;
-  if (c->nv == 3) signal_speed_kernel<3><<<nb, 256, 0, c->st>>>(U, c->ncell, c->g.gamma, dx[0], dx[1], dx[2], c->smax, c->status);
-  else if (c->nv == 4) signal_speed_kernel<4><<<nb, 256, 0, c->st>>>(U, c->ncell, c->g.gamma, dx[0], dx[1], dx[2], c->smax, c->status);
-  else signal_speed_kernel<5><<<nb, 256, 0, c->st>>>(U, c->ncell, c->g.gamma, dx[0], dx[1], dx[2], c->smax, c->status);
+  const double r0 = 1.0 / dx[0], r1 = 1.0 / dx[1], r2 = 1.0 / dx[2];
+  if (c->nv == 3) signal_speed_kernel<3><<<nb, 256, 0, c->st>>>(U, c->ncell, c->g.gamma, r0, r1, r2, c->smax, c->status);
+  else if (c->nv == 4) signal_speed_kernel<4><<<nb, 256, 0, c->st>>>(U, c->ncell, c->g.gamma, r0, r1, r2, c->smax, c->status);
+  else signal_speed_kernel<5><<<nb, 256, 0, c->st>>>(U, c->ncell, c->g.gamma, r0, r1, r2, c->smax, c->status);
   return cudaGetLastError();
 }
 
@@ -927,17 +936,13 @@ cudaError_t launch_rhs_divergence(int nv, double* const F[3], const int n[3], co
   for (int d = 0; d < 3; ++d) {
     a.F[d] = F[d];
     a.n[d] = n[d];
-    a.dx[d] = dx[d];
+    a.rdx[d] = 1.0 / dx[d];
     a.nface[d] = nface[d];
   }
   a.out = out;
   a.ncell = ncell;
   a.mode = 0;
-  unsigned nb = ew_blocks(ncell);
-  if (nv == 3) stage_kernel<3><<<nb, 256, 0, st>>>(a);
-  else if (nv == 4) stage_kernel<4><<<nb, 256, 0, st>>>(a);
-  else stage_kernel<5><<<nb, 256, 0, st>>>(a);
-  return cudaGetLastError();
+  return launch_stage_kernel(nv, a, st);
 }
 
 }  // namespace tenom
