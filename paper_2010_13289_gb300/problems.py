@@ -117,6 +117,22 @@ def solenoidal_3d(n, seed, mach=0.6, k0=4.0, gamma=GAMMA):
     return prim, dx
 
 
+def taylor_green_3d(n, gamma=GAMMA):
+    """Inviscid Taylor-Green vortex (Section 4.3.1, Eq. TGV): on [0, 2 pi]^3, n^3 points at
+    cell centres, rho = 1, u = sin x cos y cos z, v = -cos x sin y cos z, w = 0,
+    p = 100 + ((cos 2x + cos 2y)(2 + cos 2z) - 2)/16.  Returns (prim[5][n][n][n], dx)."""
+    dx = 2.0 * np.pi / n
+    x = (np.arange(n) + 0.5) * dx
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    prim = np.empty((5, n, n, n))
+    prim[0] = 1.0
+    prim[1] = np.sin(X) * np.cos(Y) * np.cos(Z)
+    prim[2] = -np.cos(X) * np.sin(Y) * np.cos(Z)
+    prim[3] = 0.0
+    prim[4] = 100.0 + ((np.cos(2 * X) + np.cos(2 * Y)) * (2.0 + np.cos(2 * Z)) - 2.0) / 16.0
+    return prim, dx
+
+
 def batch_sizes(nprob, seed, nmin=128, nmax=8192):
     """Sizes N_j = round(exp(U[ln nmin, ln nmax])) of independent 1D problems."""
     rng = np.random.default_rng(seed)
