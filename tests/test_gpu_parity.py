@@ -324,23 +324,22 @@ def test_certified_fp32_cutoff_filter_equals_fp64_decisions(T, kind, shape, bc, 
 
 
 def test_taylor_green_parity_and_conservation(T, orc):
-    """Inviscid Taylor-Green vortex (Eq. TGV) at 16^3, TENO8A-M-MP: two SSP-RK3 steps agree
-    with the oracle; over 40 steps mass, momentum and energy sums stay at rounding level
-    (flux form, periodic) and the kinetic energy stays bounded by its initial value (no
-    exchange beyond the weak pressure work of this low-Mach flow)."""
+    """Inviscid Taylor-Green vortex (Eq. TGV) at 16^3, TENO8A-M-MP: face fluxes and flags of
+    every axis agree with the oracle (the symmetric field makes many characteristic
+    stencils flat, so many cutoff decisions are set by rounding: those are the
+    noise-decided faces of the parity rules); over 40 GPU steps mass, momentum and energy
+    sums stay at rounding level (flux form, periodic) and the kinetic energy stays bounded
+    by its initial value (no exchange beyond the weak pressure work of this low-Mach flow)."""
     n = 16
     prim, dx = PB.taylor_green_3d(n)
-    S, g, so, Uo, Ug = setup(T, orc, (n, n, n), (0, 0, 0), 8, 0, prim, dx=(dx, dx, dx))
-    dto = 0.5 * orc.max_dt(g, Uo, 0.4)
-    dt = torch.tensor([dto], dtype=torch.float64, device="cuda")
-    U1o = Uo
-    for _ in range(2):
-        U1o, _ = orc.rk3_step(g, so, U1o, dto)
-    U1g = Ug.clone()
-    for _ in range(2):
-        S.rk3_step(U1g, dt)
-    err = np.abs(U1g.cpu().numpy() - U1o) / np.maximum(np.abs(U1o), 1e-3 * np.abs(U1o).max(axis=(1, 2, 3), keepdims=True))
-    assert float(np.mean(err > 1e-12)) < 0.01 and np.median(err) < 1e-15
+    shape = (n, n, n)
+    S, g, so, Uo, Ug = setup(T, orc, shape, (0, 0, 0), 8, 0, prim, dx=(dx, dx, dx))
+    for a in range(3):
+        Fg, flg = S.face_dump(Ug, a)
+        Fo, flo, cut, noise, bad, scale = orc.faces(g, so, Uo, a, with_scale=True)
+        assert bad == 0
+        compare_faces(Fg.cpu().numpy(), flg.cpu().numpy(), Fo, flo, cut, noise, scale, label="TGV axis %d" % a)
+    dt = S.max_dt(Ug, 0.4)
     U = Ug.clone()
     ke = lambda X: float((0.5 * (X[1] ** 2 + X[2] ** 2 + X[3] ** 2) / X[0]).sum())
     tot0, ke0 = U.sum(dim=(1, 2, 3)), ke(U)
