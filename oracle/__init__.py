@@ -33,7 +33,8 @@ class Grid(ctypes.Structure):
 class Scheme(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int), ("limiter", ctypes.c_int), ("ct_mode", ctypes.c_int),
                 ("ct_const", ctypes.c_double), ("mp_alpha", ctypes.c_double), ("mp_beta", ctypes.c_double),
-                ("mp_curv", ctypes.c_int), ("weights", ctypes.c_int), ("d", ctypes.c_double * 6)]
+                ("mp_curv", ctypes.c_int), ("weights", ctypes.c_int), ("d", ctypes.c_double * 6),
+                ("positivity", ctypes.c_int)]
 
 
 def make_grid(shape, dx, bc, gamma=1.4):
@@ -49,8 +50,9 @@ def make_grid(shape, dx, bc, gamma=1.4):
 
 
 def make_scheme(K=6, limiter=LIM_MP, ct_mode=None, ct_const=1e-5, mp_alpha=1.25, mp_beta=4.0,
-                mp_curv=CURV_M4, weights=W_TENOM, d=None):
-    """Defaults: K = 6 uses constant C_T = 1e-5, K = 8 the adaptive C_T of TENO8A."""
+                mp_curv=CURV_M4, weights=W_TENOM, d=None, positivity=0):
+    """Defaults: K = 6 uses constant C_T = 1e-5, K = 8 the adaptive C_T of TENO8A.
+    positivity=1: the positivity-preserving flux limiter (Section 4.4) in every RK stage."""
     s = Scheme()
     s.K = K
     s.limiter = limiter
@@ -60,6 +62,7 @@ def make_scheme(K=6, limiter=LIM_MP, ct_mode=None, ct_const=1e-5, mp_alpha=1.25,
     s.mp_beta = mp_beta
     s.mp_curv = mp_curv
     s.weights = weights
+    s.positivity = positivity
     for k in range(6):
         s.d[k] = 0.0 if d is None else (d[k] if k < len(d) else 0.0)
     return s
@@ -100,6 +103,8 @@ def lib():
         L.orc_faces.restype = c_int
         L.orc_faces_at.argtypes = [gp, sp, dp, c_int, ip, c_int, dp, u8p, dp, dp, dp]
         L.orc_faces_at.restype = c_int
+        L.orc_faces_limited.argtypes = [gp, sp, dp, c_int, c_double, dp]
+        L.orc_faces_limited.restype = c_int
         L.orc_rhs.argtypes = [gp, sp, dp, dp]
         L.orc_rhs.restype = c_int
         L.orc_max_dt.argtypes = [gp, dp, c_double]
@@ -223,6 +228,15 @@ def faces_at(grid, scheme, U, axis, idx, with_scale=False):
     if with_scale:
         return F, fl, cut, noise, bad, scale
     return F, fl, cut, noise, bad
+
+
+def faces_limited(grid, scheme, U, axis, dt):
+    """Face fluxes [nv, *face_shape] of one axis after the positivity limiter of a
+    forward-Euler stage of length dt (Section 4.4)."""
+    U = _c(U)
+    F = np.zeros((nvar(grid),) + face_shape(grid, axis))
+    bad = lib().orc_faces_limited(ctypes.byref(grid), ctypes.byref(scheme), _d(U), axis, dt, _d(F))
+    return F, bad
 
 
 def rhs(grid, scheme, U):

@@ -106,6 +106,16 @@ int orc_faces_at(const Grid* g, const Scheme* s, const double* U, int axis, cons
   return bad;
 }
 
+/* Face fluxes of one axis after the positivity limiter of a forward-Euler stage of
+   length dt (Section 4.4); the scheme's positivity flag is not consulted. */
+int orc_faces_limited(const Grid* g, const Scheme* s, const double* U, int axis, double dt, double* Fhat) {
+  Grid G = norm_grid(g);
+  Scheme S = norm_scheme(s);
+  int bad = all_faces<double>(G, S, U, axis, Fhat, nullptr, nullptr, nullptr);
+  positivity_limit(G, U, axis, dt, Fhat);
+  return bad;
+}
+
 int orc_rhs(const Grid* g, const Scheme* s, const double* U, double* dUdt) {
   Grid G = norm_grid(g);
   Scheme S = norm_scheme(s);

@@ -12,12 +12,16 @@
      - orc::Counted    (counts FP64 operations: the algorithmic flop figure).
 
    Readings of points the paper leaves open are marked "reading:" where used.
+   The positivity-preserving flux limiter (Section 4.4) is pinned by
+   tests/test_oracle_positivity.py (segment and floor properties, exactness where it is
+   inactive, conservation, Le Blanc against the exact Riemann solution).
    Parity-unpinned parts (no printed example exists): the adaptive cutoff C_T of
    TENO8A (Eqs. shock_indicator, cut-off_adjust) beyond its printed constants. */
 #pragma once
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 #include "beta_forms.h"
 
@@ -93,6 +97,7 @@ struct Scheme {
   int weights;      /* W_TENOM: Eq. reconstuction with w_k = d_k (Section 3.3);
                        W_TENO: standard renormalised weights, Eq. weight_renormalize */
   double d[6];      /* optimal linear weights d_k */
+  int positivity;   /* 1: positivity-preserving flux limiter in every RK stage (Section 4.4) */
 };
 
 /* Optimal linear weights.  The paper does not print them (Section 3.3 allows
@@ -634,10 +639,94 @@ inline int all_faces(const Grid& g, const Scheme& S, const T* U, int a, T* Fhat,
   return bad;
 }
 
+/* ------------------------------------------------------------------ positivity */
+/* Pressure (gamma - 1) (E - |m|^2 / (2 rho)) of one conserved state. */
+inline double pressure_of(const Grid& g, const double* W) {
+  const int nv = g.dim + 2;
+  double m2 = 0.0;
+  for (int d = 0; d < g.dim; ++d) m2 += W[1 + d] * W[1 + d];
+  return (g.gamma - 1.0) * (W[nv - 1] - 0.5 * m2 / W[0]);
+}
+
+/* Positivity-preserving flux limiter that Section 4.4 applies (Hu, Adams & Shu,
+   J. Comput. Phys. 242, 2013), for one forward-Euler stage of length dt, on the face
+   fluxes Fh ([nv][nface]) of axis a computed from U.
+   The stage update U_i - sum_a lambda_a (F_{a,i+1/2} - F_{a,i-1/2}), lambda_a = dt/dx_a,
+   is the mean of the 2D one-sided states U_i - mu_a F_{a,i+1/2} and U_i + mu_a F_{a,i-1/2}
+   with mu_a = 2 D lambda_a; each stays admissible when its face flux is the first-order
+   Lax-Friedrichs flux F^LF = (F(U_L) + F(U_R) - alpha (U_R - U_L)) / 2 and the step is small
+   enough.  The face flux becomes F^LF + theta (F^H - F^LF), F^H the high-order flux:
+     theta_rho: on each side, if the density of the one-sided state made with F^H is below
+       eps = min(1e-13, density made with F^LF), the theta at which the (linear) density
+       equals eps; the smaller of the two sides, else 1;
+     theta_p: the same for the pressure, with F^H replaced by the density-limited flux
+       F1 = F^LF + theta_rho (F^H - F^LF); the pressure is concave in the state, so the
+       theta where (1 - theta) p(F^LF state) + theta p(F1 state) = eps keeps it >= eps;
+     flux = F^LF + theta_p (F1 - F^LF);
+   theta = 1 leaves the flux it would scale as it is (no rounding of an unlimited face).
+   Readings: alpha = max of |u_a| + c over the two cells of the face (local Lax-Friedrichs);
+   eps as above; the 1/(2D) split; the outside cell of a transmissive boundary face (the
+   boundary's copy of the edge cell) is checked like an interior one. */
+inline void positivity_limit(const Grid& g, const double* U, int a, double dt, double* Fh) {
+  const int D = g.dim, nv = D + 2;
+  const long long nc = ncell(g), nf = nface(g, a);
+  const long long stride[3] = {1, g.n[0], (long long)g.n[0] * g.n[1]};
+  int fn[3] = {1, 1, 1};
+  for (int d = 0; d < D; ++d) fn[d] = (d == a) ? g.n[d] + 1 : g.n[d];
+  const double mu = 2.0 * D * dt / g.dx[a];
+  for (int z = 0; z < fn[2]; ++z)
+    for (int y = 0; y < fn[1]; ++y)
+      for (int x = 0; x < fn[0]; ++x) {
+        const int idx[3] = {x, y, z};
+        const long long lin = x + (long long)fn[0] * (y + (long long)fn[1] * z);
+        double Us[2][5], Fc[2][5], sp[2];
+        for (int side = 0; side < 2; ++side) {
+          const int j = bc_index(g, a, idx[a] - 1 + side); /* cell left (0) or right (1) of the face */
+          long long cl = 0;
+          for (int d = 0; d < D; ++d) cl += (long long)((d == a) ? j : idx[d]) * stride[d];
+          for (int v = 0; v < nv; ++v) Us[side][v] = U[v * nc + cl];
+          Point<double> P;
+          point_from_U(g, Us[side], &P);
+          phys_flux(g, P, a, Fc[side]);
+          sp[side] = std::fabs(P.vel[a]) + P.c;
+        }
+        const double alpha = std::fmax(sp[0], sp[1]);
+        double FLF[5], FH[5], F1[5];
+        for (int v = 0; v < nv; ++v) {
+          FLF[v] = 0.5 * (Fc[0][v] + Fc[1][v] - alpha * (Us[1][v] - Us[0][v]));
+          FH[v] = Fh[v * nf + lin];
+        }
+        const double sgn_mu[2] = {-mu, mu}; /* left cell loses F, right cell gains it */
+        double th = 1.0;
+        for (int side = 0; side < 2; ++side) {
+          const double rlf = Us[side][0] + sgn_mu[side] * FLF[0];
+          const double rh = Us[side][0] + sgn_mu[side] * FH[0];
+          const double eps = std::fmin(1e-13, rlf);
+          if (rh < eps) th = std::fmin(th, (rlf - eps) / (rlf - rh));
+        }
+        for (int v = 0; v < nv; ++v) F1[v] = (th == 1.0) ? FH[v] : FLF[v] + th * (FH[v] - FLF[v]);
+        double tp = 1.0;
+        for (int side = 0; side < 2; ++side) {
+          double Wlf[5], W1[5];
+          for (int v = 0; v < nv; ++v) {
+            Wlf[v] = Us[side][v] + sgn_mu[side] * FLF[v];
+            W1[v] = Us[side][v] + sgn_mu[side] * F1[v];
+          }
+          const double plf = pressure_of(g, Wlf), p1 = pressure_of(g, W1);
+          const double eps = std::fmin(1e-13, plf);
+          if (p1 < eps) tp = std::fmin(tp, (plf - eps) / (plf - p1));
+        }
+        if (tp < 1.0 || th < 1.0)
+          for (int v = 0; v < nv; ++v) Fh[v * nf + lin] = (tp == 1.0) ? F1[v] : FLF[v] + tp * (F1[v] - FLF[v]);
+      }
+}
+
 /* Semi-discrete operator dU/dt = -sum_a (F_{a,i+1/2} - F_{a,i-1/2}) / dx_a
-   (Eq. approximateEq, dimension by dimension as in Section 4). */
+   (Eq. approximateEq, dimension by dimension as in Section 4).  With pp_dt > 0 and
+   S.positivity set, the face fluxes first pass the positivity limiter of a forward-Euler
+   stage of length pp_dt (FP64 only). */
 template <class T>
-inline int rhs(const Grid& g, const Scheme& S, const T* U, T* dUdt) {
+inline int rhs(const Grid& g, const Scheme& S, const T* U, T* dUdt, double pp_dt = 0.0) {
   const int D = g.dim, nv = D + 2;
   long long nc = ncell(g);
   for (long long q = 0; q < nv * nc; ++q) dUdt[q] = 0.0;
@@ -646,6 +735,8 @@ inline int rhs(const Grid& g, const Scheme& S, const T* U, T* dUdt) {
     long long nf = nface(g, a);
     std::vector<T> Fh((size_t)nv * nf);
     bad |= all_faces<T>(g, S, U, a, Fh.data(), nullptr, nullptr, nullptr);
+    if constexpr (std::is_same<T, double>::value)
+      if (S.positivity && pp_dt > 0.0) positivity_limit(g, U, a, pp_dt, Fh.data());
     int fn[3] = {1, 1, 1};
     for (int d = 0; d < D; ++d) fn[d] = (d == a) ? g.n[d] + 1 : g.n[d];
     long long fstride = 1;
@@ -708,11 +799,12 @@ inline int rk3_step(const Grid& g, const Scheme& S, T* U, T dt) {
   const int nv = g.dim + 2;
   long long N = nv * ncell(g);
   std::vector<T> L(N), U1(N), U2(N);
-  int bad = rhs<T>(g, S, U, L.data());
+  /* each stage is a forward-Euler step of length dt (the positivity limiter's lambda) */
+  int bad = rhs<T>(g, S, U, L.data(), val(dt));
   for (long long q = 0; q < N; ++q) U1[q] = U[q] + dt * L[q];
-  bad |= rhs<T>(g, S, U1.data(), L.data());
+  bad |= rhs<T>(g, S, U1.data(), L.data(), val(dt));
   for (long long q = 0; q < N; ++q) U2[q] = 0.75 * U[q] + 0.25 * (U1[q] + dt * L[q]);
-  bad |= rhs<T>(g, S, U2.data(), L.data());
+  bad |= rhs<T>(g, S, U2.data(), L.data(), val(dt));
   for (long long q = 0; q < N; ++q) U[q] = 1.0 / 3.0 * U[q] + 2.0 / 3.0 * (U2[q] + dt * L[q]);
   return bad;
 }

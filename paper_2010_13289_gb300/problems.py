@@ -13,6 +13,9 @@ Workloads (shaped like the paper's Section 4 problems):
                     E(k) ~ k^4 exp(-2 (k/4)^2), rms Mach 0.6, rho = 1, p = 1/gamma
   batch_sizes       log-uniform sizes 128..8192 for batched 1D problems
   gaussian_pulse    exp(-300 (x - 0.5)^2) on [0,1] (Section 4.1.1)
+  taylor_green_3d   inviscid Taylor-Green vortex (Section 4.3.1)
+  le_blanc_1d       Le Blanc shock tube on [0,9], gamma = 5/3 (Section 4.4.2)
+  near_vacuum       seeded blocks of density 1e-3..1 and pressure 1e-10..1e-1
 """
 import numpy as np
 
@@ -131,6 +134,41 @@ def taylor_green_3d(n, gamma=GAMMA):
     prim[3] = 0.0
     prim[4] = 100.0 + ((np.cos(2 * X) + np.cos(2 * Y)) * (2.0 + np.cos(2 * Z)) - 2.0) / 16.0
     return prim, dx
+
+
+LE_BLANC_GAMMA = 5.0 / 3.0
+LE_BLANC_LEFT = (1.0, 0.0, 2.0 / 3.0 * 1e-1)
+LE_BLANC_RIGHT = (1e-3, 0.0, 2.0 / 3.0 * 1e-10)
+
+
+def le_blanc_1d(n):
+    """Le Blanc problem (Section 4.4.2, Eq. Leblanc): on [0, 9], (rho, u, p) = (1, 0, 2/3 1e-1)
+    for x < 3 and (1e-3, 0, 2/3 1e-10) for x >= 3, n cells; gamma = 5/3, run to t = 6.
+    Returns (prim[3][n], dx)."""
+    return riemann_1d(n, 0, x0=0.0, x1=9.0, xc=3.0, states=(LE_BLANC_LEFT, LE_BLANC_RIGHT))
+
+
+def near_vacuum(shape, seed, block=4):
+    """Seeded state of piecewise-constant blocks (block^D cells) with log-uniform density
+    in [1e-3, 1], pressure in [1e-10, 1e-1] and velocity components in [-1, 1]: every block
+    edge is a strong jump next to near-vacuum.  shape = (nz, ny, nx) trailing dims.
+    Returns prim[D+2][*shape]."""
+    rng = np.random.default_rng(seed)
+    D = len(shape)
+    nb = [-(-n // block) for n in shape]
+    rho = 10.0 ** rng.uniform(-3.0, 0.0, nb)
+    p = 10.0 ** rng.uniform(-10.0, -1.0, nb)
+    vel = rng.uniform(-1.0, 1.0, [D] + nb)
+    def expand(a):
+        for ax in range(D):
+            a = np.repeat(a, block, axis=ax)
+        return a[tuple(slice(0, n) for n in shape)]
+    prim = np.empty((D + 2,) + tuple(shape))
+    prim[0] = expand(rho)
+    for d in range(D):
+        prim[1 + d] = expand(vel[d])
+    prim[D + 1] = expand(p)
+    return prim
 
 
 def batch_sizes(nprob, seed, nmin=128, nmax=8192):
