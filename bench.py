@@ -659,6 +659,84 @@ def run_tgv(args):
     S.close()
 
 
+def run_le_blanc(args):
+    """Le Blanc problem (Section 4.4.2, Eq. Leblanc): 900 cells on [0, 9], gamma = 5/3,
+    TENO8-MP with the minmod curvature and beta = 1 and the positivity-preserving flux
+    limiter (Section 4.4), CFL 0.4, to t = 6, timed end to end on the device (a 900-cell
+    grid is launch-bound: about 16 launches per step).  Also times the limiter's cost on the
+    2D 2048^2 broadband workload: step time with the limiter over step time without."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2010_13289_gb300 import problems as PB
+    from paper_2010_13289_gb300 import tenom as T
+    n, t_final = 900, 6.0
+    prim, dx = PB.le_blanc_1d(n)
+    gam = PB.LE_BLANC_GAMMA
+    sch = T.make_scheme(8, limiter=T.LIM_MP, mp_curv=T.CURV_MM, mp_beta=1.0, positivity=T.PP_ON)
+    S = T.Solver((n,), (dx,), (T.BC_TRANSMISSIVE,), sch, gamma=gam)
+    primd = torch.from_numpy(prim).cuda()
+    t = torch.zeros(1, dtype=torch.float64, device="cuda")
+    # untimed pass: count the steps to t_final
+    U = S.init_state(primd)
+    steps = 0
+    while t.item() < t_final:
+        S.advance(U, 1, t_end=t_final, cfl=0.4, t_dev=t)
+        steps += 1
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(0)
+    clocks.start()
+    runs = []
+    for _ in range(max(1, args.steps // 5)):
+        U = S.init_state(primd)
+        t.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        S.advance(U, steps, t_end=t_final, cfl=0.4, t_dev=t)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        runs.append(e0.elapsed_time(e1))
+    assert t.item() == t_final
+    Un = U.cpu().numpy()
+    p = (gam - 1.0) * (Un[2] - 0.5 * Un[1] ** 2 / Un[0])
+    st = S.status()
+    S.close()
+    # the limiter's cost on a large grid
+    prim2, dx2 = make_prim("broadband_2d_2048_teno6_mp", args.seed)
+    prim2d = torch.from_numpy(prim2).cuda()
+    ms2 = {}
+    for label, pp in (("off", T.PP_OFF), ("on", T.PP_ON)):
+        S2 = T.Solver((2048, 2048), dx2, (T.BC_PERIODIC,) * 2, T.make_scheme(6, positivity=pp))
+        U2 = S2.init_state(prim2d)
+        S2.advance(U2, args.warmup)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        S2.advance(U2, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms2[label] = e0.elapsed_time(e1) / args.steps
+        S2.close()
+    clk = clocks.stop()
+    ms = statistics.median(runs)
+    out = {"metric": "cell-updates/s per RK stage (FP64)", "value": float(n) * 3 * steps / (ms * 1e-3),
+           "unit": "cell-updates/s", "n_gpus": 1, "steps": steps, "warmup": 1, "ms_per_step": ms / steps,
+           "higher_is_better": True, "dtype": "f64", "data": "analytic initial condition (Eq. Leblanc)",
+           "config": {"workload": "le_blanc_1d_900_teno8_mp_pp", "shape": [n], "K": 8, "limiter": "MP",
+                      "mp_curv": "minmod", "mp_beta": 1.0, "positivity": True, "gamma": gam,
+                      "t_final": t_final, "cfl": 0.4},
+           "time_to_t_final_ms": ms, "timed_runs": len(runs),
+           "final_state": {"min_rho": float(Un[0].min()), "min_p": float(p.min()),
+                           "finite": bool(np.isfinite(Un).all()), "status_word": int(st)},
+           "limiter_cost_2d_2048_teno6_mp": {"ms_per_step_off": ms2["off"], "ms_per_step_on": ms2["on"],
+                                             "ratio": ms2["on"] / ms2["off"]},
+           "clocks": clk}
+    print(json.dumps(out), flush=True)
+
+
 def run_adjoint(args):
     """Adjoint workload: 2D 512^2 broadband field with circular jumps, TENO6-MP, 200 SSP-RK3
     steps at a fixed dt, loss = integral of p over a seeded 64 x 64 window at the end;
@@ -761,7 +839,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT,
-                    choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(ADJOINT_WORKLOADS) + ["cost_ratios_2d_2048", "tgv_3d_64_teno8_mp"])
+                    choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS) + sorted(ADJOINT_WORKLOADS) + ["cost_ratios_2d_2048", "tgv_3d_64_teno8_mp", "le_blanc_1d_900_teno8_mp_pp"])
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--ref-seconds", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -784,6 +862,8 @@ def main():
         run_cost_ratios(args)
     elif args.workload == "tgv_3d_64_teno8_mp":
         run_tgv(args)
+    elif args.workload == "le_blanc_1d_900_teno8_mp_pp":
+        run_le_blanc(args)
     else:
         run_ours(args)
 

@@ -84,8 +84,23 @@ typedef struct tenom_scheme {
   int decisions;    /* TENOM_DECIDE_FILTERED (default): cutoff decisions certified in FP32 and
                        decided in FP64 where the FP32 bounds do not settle them (same outcome
                        as FP64); TENOM_DECIDE_FP64: FP64 only */
-  int reserved;
+  int positivity;   /* TENOM_PP_OFF (default) or TENOM_PP_ON: the positivity-preserving flux
+                       limiter that Section 4.4 applies (Hu, Adams & Shu 2013).  It belongs to a
+                       forward-Euler stage of length dt, so it acts in the stepping calls
+                       (tenom_rk3_step, tenom_advance, tenom_advance_host: in every SSP-RK3
+                       stage, with that step's dt); tenom_rhs, tenom_rhs_noalloc and
+                       tenom_face_dump return the unlimited operator; the adjoint calls return
+                       TENOM_E_UNSUPPORTED and tenom_batch_create rejects it.  Per face of axis
+                       a the high-order flux F^H is pulled towards the local Lax-Friedrichs flux
+                       F^LF = (F(U_L) + F(U_R) - alpha (U_R - U_L))/2, alpha = max(|u_a| + c) of
+                       the two cells: F = F^LF + theta (F^H - F^LF), theta in [0, 1] the product
+                       of a density factor and a pressure factor chosen so that both one-sided
+                       states U_L - mu F and U_R + mu F (mu = 2 dim dt/dx_a) keep density and
+                       pressure >= min(1e-13, their value with F^LF); theta = 1 leaves F^H
+                       untouched. */
 } tenom_scheme;
+
+enum { TENOM_PP_OFF = 0, TENOM_PP_ON = 1 };
 
 enum { TENOM_DECIDE_FILTERED = 0, TENOM_DECIDE_FP64 = 1 };
 
@@ -128,6 +143,15 @@ tenom_status tenom_advance(tenom_ctx* ctx, double* U, double* t_dev, double t_en
  * run tenom_advance from t = *t_host, copy the state and t back, synchronise. */
 tenom_status tenom_advance_host(tenom_ctx* ctx, const double* U_host_in, double* U_host_out, double* t_host,
                                 double t_end, double cfl, int nsteps);
+
+/* The positivity-preserving flux limiter of one forward-Euler stage of length *dt_dev
+ * (Section 4.4; see tenom_scheme.positivity) applied in place to face fluxes Fhat of axis
+ * `axis` (device [nvar][nface_a], layout of tenom_face_dump) at the state U (device
+ * [nvar][ncell]).  The stepping calls apply the same kernel to their own fluxes when the
+ * scheme asks for it; this call applies it whatever the scheme's flag, to fluxes the caller
+ * supplies.  A face whose blend factors are both 1 is left bit for bit.  dt_dev <= 0 leaves
+ * Fhat unchanged.  Returns TENOM_E_INVALID for a bad axis or pointer. */
+tenom_status tenom_positivity_limit(tenom_ctx* ctx, const double* U, int axis, const double* dt_dev, double* Fhat);
 
 /* Diagnostic face dump of axis a for parity checks: the same kernel as the solver writes
  * Fhat (device [nvar][nface_a]) and per face, field s and split side (0: f+, 1: f-) one

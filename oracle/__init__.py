@@ -105,6 +105,7 @@ def lib():
         L.orc_faces_at.restype = c_int
         L.orc_faces_limited.argtypes = [gp, sp, dp, c_int, c_double, dp]
         L.orc_faces_limited.restype = c_int
+        L.orc_positivity_limit.argtypes = [gp, dp, c_int, c_double, dp]
         L.orc_rhs.argtypes = [gp, sp, dp, dp]
         L.orc_rhs.restype = c_int
         L.orc_max_dt.argtypes = [gp, dp, c_double]
@@ -237,6 +238,14 @@ def faces_limited(grid, scheme, U, axis, dt):
     F = np.zeros((nvar(grid),) + face_shape(grid, axis))
     bad = lib().orc_faces_limited(ctypes.byref(grid), ctypes.byref(scheme), _d(U), axis, dt, _d(F))
     return F, bad
+
+
+def positivity_limit(grid, U, axis, dt, F):
+    """The positivity limiter (Section 4.4) applied to given face fluxes F[nv, *face_shape]
+    of one axis; returns the limited copy."""
+    F = _c(F).copy()
+    lib().orc_positivity_limit(ctypes.byref(grid), _d(_c(U)), axis, dt, _d(F))
+    return F
 
 
 def rhs(grid, scheme, U):

@@ -116,6 +116,13 @@ int orc_faces_limited(const Grid* g, const Scheme* s, const double* U, int axis,
   return bad;
 }
 
+/* The positivity limiter of a forward-Euler stage of length dt on caller-given face
+   fluxes Fhat ([nv][nface]) of one axis, in place. */
+void orc_positivity_limit(const Grid* g, const double* U, int axis, double dt, double* Fhat) {
+  Grid G = norm_grid(g);
+  positivity_limit(G, U, axis, dt, Fhat);
+}
+
 int orc_rhs(const Grid* g, const Scheme* s, const double* U, double* dUdt) {
   Grid G = norm_grid(g);
   Scheme S = norm_scheme(s);

@@ -194,6 +194,141 @@ __global__ void prim_kernel(const double* __restrict__ U, long long ncell, doubl
   if (st) atomicOr(status, st);
 }
 
+/* Positivity-preserving flux limiter of one forward-Euler stage of length dt (Section 4.4,
+   which applies the limiter of Hu, Adams & Shu 2013), in place on the face fluxes of one
+   axis.  One thread per face.  The stage update is the mean of the one-sided states
+   U_L - mu F (cell left of the face) and U_R + mu F (cell right), mu = 2 dim dt/dx_a, over
+   the 2 dim faces of a cell; the face flux F^H is pulled towards the local Lax-Friedrichs
+   flux F^LF = (F(U_L) + F(U_R) - alpha (U_R - U_L))/2, alpha = max(|u_a| + c) of the two
+   cells, until both one-sided states keep density (a linear function of the blend factor,
+   solved exactly) and then pressure (concave in the state, so the chord bound is safe)
+   at or above eps = min(1e-13, the value with F^LF).  A face whose factors are both 1 is
+   not rewritten.  The cell outside a transmissive boundary is the boundary's copy of the
+   edge cell, checked like an interior one. */
+struct PosArgs {
+  const double* U;
+  double* F;           /* face fluxes of the axis, [NV][nface] */
+  const double* dt;    /* device dt of the stage */
+  int n[3];
+  int bc[3];
+  int axis;
+  double mu_per_dt;    /* 2 dim / dx_a */
+  double gamma;
+};
+
+template <int NV>
+__device__ __forceinline__ double state_pressure(const double (&W)[NV], double gm1) {
+  double m2 = 0.0;
+#pragma unroll
+  for (int d = 1; d < NV - 1; ++d) m2 += W[d] * W[d];
+  return gm1 * (W[NV - 1] - 0.5 * m2 / W[0]);
+}
+
+template <int NV>
+__global__ void positivity_kernel(const PosArgs A) {
+  const double dt = *A.dt;
+  if (!(dt > 0.0)) return;  /* a step past t_end: nothing moves */
+  const int a = A.axis;
+  int fn[3] = {A.n[0], A.n[1], A.n[2]};
+  fn[a] += 1;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= fn[0]) return;
+  const long long ncell = (long long)A.n[0] * A.n[1] * A.n[2];
+  const long long nface = (long long)fn[0] * fn[1] * fn[2];
+  const double mu = A.mu_per_dt * dt;
+  const double gm1 = A.gamma - 1.0;
+  const int na = A.n[a];
+  const long long cstride = (a == 0) ? 1 : (a == 1 ? (long long)A.n[0] : (long long)A.n[0] * A.n[1]);
+  for (int z = blockIdx.z; z < fn[2]; z += gridDim.z) {
+    for (int y = blockIdx.y; y < fn[1]; y += gridDim.y) {
+      const long long lin = x + (long long)fn[0] * (y + (long long)fn[1] * z);
+      int idx[3] = {x, y, z};
+      const int f = idx[a];
+      int jl = f - 1, jr = f;
+      if (A.bc[a] == TENOM_BC_PERIODIC) {
+        if (jl < 0) jl += na;
+        if (jr >= na) jr -= na;
+      } else {
+        if (jl < 0) jl = 0;
+        if (jr > na - 1) jr = na - 1;
+      }
+      idx[a] = 0;
+      const long long base = idx[0] + (long long)A.n[0] * (idx[1] + (long long)A.n[1] * idx[2]);
+      const long long cell[2] = {base + jl * cstride, base + jr * cstride};
+      double Us[2][NV], Fc[2][NV], sp[2];
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Us[sd][v] = A.U[v * ncell + cell[sd]];
+        const double rho = Us[sd][0];
+        double vel[NV - 2], ke = 0.0;
+#pragma unroll
+        for (int d = 0; d < NV - 2; ++d) {
+          vel[d] = Us[sd][1 + d] / rho;
+          ke += Us[sd][1 + d] * vel[d];
+        }
+        const double p = gm1 * (Us[sd][NV - 1] - 0.5 * ke);
+        const double un = vel[a];
+        Fc[sd][0] = Us[sd][1 + a];
+#pragma unroll
+        for (int d = 0; d < NV - 2; ++d) Fc[sd][1 + d] = Us[sd][1 + d] * un + (d == a ? p : 0.0);
+        Fc[sd][NV - 1] = (Us[sd][NV - 1] + p) * un;
+        sp[sd] = fabs(un) + sqrt(A.gamma * p / rho);
+      }
+      const double alpha = fmax(sp[0], sp[1]);
+      double FLF[NV], FH[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        FLF[v] = 0.5 * (Fc[0][v] + Fc[1][v] - alpha * (Us[1][v] - Us[0][v]));
+        FH[v] = A.F[v * nface + lin];
+      }
+      /* density factor over both one-sided states (left loses F, right gains it) */
+      double th = 1.0;
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        const double m = sd ? mu : -mu;
+        const double rlf = Us[sd][0] + m * FLF[0];
+        const double rh = Us[sd][0] + m * FH[0];
+        const double eps = fmin(1e-13, rlf);
+        if (rh < eps) th = fmin(th, (rlf - eps) / (rlf - rh));
+      }
+      double F1[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) F1[v] = (th == 1.0) ? FH[v] : FLF[v] + th * (FH[v] - FLF[v]);
+      /* pressure factor on the density-limited flux */
+      double tp = 1.0;
+#pragma unroll
+      for (int sd = 0; sd < 2; ++sd) {
+        const double m = sd ? mu : -mu;
+        double Wlf[NV], W1[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          Wlf[v] = Us[sd][v] + m * FLF[v];
+          W1[v] = Us[sd][v] + m * F1[v];
+        }
+        const double plf = state_pressure<NV>(Wlf, gm1), p1 = state_pressure<NV>(W1, gm1);
+        const double eps = fmin(1e-13, plf);
+        if (p1 < eps) tp = fmin(tp, (plf - eps) / (plf - p1));
+      }
+      if (th < 1.0 || tp < 1.0) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) A.F[v * nface + lin] = (tp == 1.0) ? F1[v] : FLF[v] + tp * (F1[v] - FLF[v]);
+      }
+    }
+  }
+}
+
+static cudaError_t launch_positivity_kernel(int nv, const PosArgs& p, cudaStream_t st) {
+  int fn[3] = {p.n[0], p.n[1], p.n[2]};
+  fn[p.axis] += 1;
+  const dim3 grid((unsigned)((fn[0] + 127) / 128), (unsigned)(fn[1] < 65535 ? fn[1] : 65535),
+                  (unsigned)(fn[2] < 65535 ? fn[2] : 65535));
+  if (nv == 3) positivity_kernel<3><<<grid, 128, 0, st>>>(p);
+  else if (nv == 4) positivity_kernel<4><<<grid, 128, 0, st>>>(p);
+  else positivity_kernel<5><<<grid, 128, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
 __global__ void fastmath_check_kernel(const double* x, double* out, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double v = x[i];
@@ -339,6 +474,7 @@ static tenom_status validate(const tenom_grid* g, const tenom_scheme* s, std::st
   if (s->ct_mode != TENOM_CT_CONST && s->ct_mode != TENOM_CT_ADAPTIVE) { *msg = "bad ct_mode"; return TENOM_E_INVALID; }
   if (s->mp_curv != TENOM_CURV_M4 && s->mp_curv != TENOM_CURV_MM) { *msg = "bad mp_curv"; return TENOM_E_INVALID; }
   if (s->weights != TENOM_W_TENOM && s->weights != TENOM_W_TENO) { *msg = "bad weights"; return TENOM_E_INVALID; }
+  if (s->positivity != TENOM_PP_OFF && s->positivity != TENOM_PP_ON) { *msg = "bad positivity flag"; return TENOM_E_INVALID; }
   if (s->decisions != TENOM_DECIDE_FILTERED && s->decisions != TENOM_DECIDE_FP64) {
     *msg = "bad decisions mode";
     return TENOM_E_INVALID;
@@ -555,13 +691,46 @@ tenom_status tenom_max_dt(tenom_ctx* c, const double* U, double cfl, double* dt_
   return e == cudaSuccess ? TENOM_OK : cuda_fail(c, e, "max_dt");
 }
 
+/* the positivity limiter on the face fluxes F of axis a, computed from the state Us, for a
+   forward-Euler stage of length *dt */
+static cudaError_t launch_positivity_axis(tenom_ctx* c, const double* Us, int a, const double* dt, double* F) {
+  PosArgs p;
+  memset(&p, 0, sizeof(p));
+  p.U = Us;
+  p.F = F;
+  p.dt = dt;
+  for (int d = 0; d < 3; ++d) {
+    p.n[d] = c->g.n[d];
+    p.bc[d] = c->g.bc[d];
+  }
+  p.axis = a;
+  p.mu_per_dt = 2.0 * c->g.dim / c->g.dx[a];
+  p.gamma = c->g.gamma;
+  return launch_positivity_kernel(c->nv, p, c->st);
+}
+
+/* the positivity limiter on every axis's face fluxes of the stage at Us (length c->dt) */
+static cudaError_t launch_positivity(tenom_ctx* c, const double* Us) {
+  cudaError_t e = cudaSuccess;
+  for (int a = 0; a < c->g.dim && e == cudaSuccess; ++a) e = launch_positivity_axis(c, Us, a, c->dt, c->face[a]);
+  return e;
+}
+
+/* face fluxes of one SSP-RK3 stage at Us: the high-order fluxes, limited when the scheme
+   asks for positivity */
+static cudaError_t stage_faces(tenom_ctx* c, const double* Us) {
+  cudaError_t e = eval_faces(c, Us);
+  if (e == cudaSuccess && c->s.positivity == TENOM_PP_ON) e = launch_positivity(c, Us);
+  return e;
+}
+
 /* three stages; dt already in c->dt */
 static cudaError_t rk3_core(tenom_ctx* c, double* U) {
-  cudaError_t e = eval_faces(c, U);
+  cudaError_t e = stage_faces(c, U);
   if (e == cudaSuccess) e = launch_stage(c, nullptr, U, c->W1, 1, 0.0, 1.0);
-  if (e == cudaSuccess) e = eval_faces(c, c->W1);
+  if (e == cudaSuccess) e = stage_faces(c, c->W1);
   if (e == cudaSuccess) e = launch_stage(c, U, c->W1, c->W1, 2, 0.75, 0.25);
-  if (e == cudaSuccess) e = eval_faces(c, c->W1);
+  if (e == cudaSuccess) e = stage_faces(c, c->W1);
   if (e == cudaSuccess) e = launch_stage(c, U, c->W1, U, 2, 1.0 / 3.0, 2.0 / 3.0);
   return e;
 }
@@ -614,6 +783,14 @@ tenom_status tenom_advance_host(tenom_ctx* c, const double* U_in, double* U_out,
     if (e != cudaSuccess) return cuda_fail(c, e, "advance_host");
   }
   return s;
+}
+
+tenom_status tenom_positivity_limit(tenom_ctx* c, const double* U, int axis, const double* dt_dev, double* Fhat) {
+  if (!c) return TENOM_E_INVALID;
+  if (axis < 0 || axis >= c->g.dim) return fail(c, TENOM_E_INVALID, "positivity_limit: bad axis");
+  if (!aligned8(U) || !aligned8(dt_dev) || !aligned8(Fhat)) return fail(c, TENOM_E_INVALID, "positivity_limit: bad pointers");
+  cudaError_t e = launch_positivity_axis(c, U, axis, dt_dev, Fhat);
+  return e == cudaSuccess ? TENOM_OK : cuda_fail(c, e, "positivity_limit");
 }
 
 tenom_status tenom_face_dump(tenom_ctx* c, const double* U, int axis, double* Fhat, uint8_t* flags) {
@@ -673,11 +850,18 @@ static size_t flags_offset(const tenom_ctx* c, int axis) {
 
 /* The frozen-branch adjoint covers the limiters whose filtered candidate is a selection
    among linear forms (MP, TVD5); the Van Albada flux is a smooth nonlinear function of the
-   stencil and has no frozen linear form here. */
+   stencil and has no frozen linear form here, nor has the positivity limiter's blend
+   factor (a ratio of the states' densities and pressures). */
 static bool adjoint_unsupported(tenom_ctx* c, const char* what) {
-  if (c->s.limiter != TENOM_LIM_VA) return false;
-  fail(c, TENOM_E_UNSUPPORTED, std::string(what) + ": no adjoint for the Van Albada limiter");
-  return true;
+  if (c->s.limiter == TENOM_LIM_VA) {
+    fail(c, TENOM_E_UNSUPPORTED, std::string(what) + ": no adjoint for the Van Albada limiter");
+    return true;
+  }
+  if (c->s.positivity == TENOM_PP_ON) {
+    fail(c, TENOM_E_UNSUPPORTED, std::string(what) + ": no adjoint for the positivity limiter");
+    return true;
+  }
+  return false;
 }
 
 /* doubles of the linearisation one stage records for one face: NV x (2K + 2) */

@@ -321,6 +321,7 @@ tenom_status tenom_batch_create(tenom_batch** out, int nprob, const int* n, cons
   if (scheme->K != 6 && scheme->K != 8) return bfail(nullptr, TENOM_E_INVALID, "K must be 6 or 8");
   if (scheme->limiter != TENOM_LIM_MP && scheme->limiter != TENOM_LIM_TVD5)
     return bfail(nullptr, TENOM_E_UNSUPPORTED, "limiter not built");
+  if (scheme->positivity != TENOM_PP_OFF) return bfail(nullptr, TENOM_E_UNSUPPORTED, "positivity limiter not built");
   tenom_batch* b = new tenom_batch();
   b->P = nprob;
   b->s = *scheme;

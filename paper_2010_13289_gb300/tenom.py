@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libtenom.so")
 TENOM_OK, TENOM_E_INVALID, TENOM_E_CUDA, TENOM_E_NONPHYSICAL, TENOM_E_TIMEOUT, TENOM_E_UNSUPPORTED = range(6)
 BC_PERIODIC, BC_TRANSMISSIVE = 0, 1
 LIM_MP, LIM_TVD5, LIM_VA = 0, 1, 2
+PP_OFF, PP_ON = 0, 1
 CT_CONST, CT_ADAPTIVE = 0, 1
 CURV_M4, CURV_MM = 0, 1
 W_TENOM, W_TENO = 0, 1
@@ -31,7 +32,7 @@ class tenom_scheme(ctypes.Structure):
     _fields_ = [("K", ctypes.c_int), ("limiter", ctypes.c_int), ("ct_mode", ctypes.c_int),
                 ("ct_const", ctypes.c_double), ("mp_alpha", ctypes.c_double), ("mp_beta", ctypes.c_double),
                 ("mp_curv", ctypes.c_int), ("weights", ctypes.c_int), ("d", ctypes.c_double * 6),
-                ("decisions", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("decisions", ctypes.c_int), ("positivity", ctypes.c_int)]
 
 
 DECIDE_FILTERED, DECIDE_FP64 = 0, 1
@@ -65,6 +66,7 @@ def lib():
         L.tenom_advance.argtypes = [VP, VP, VP, c_double, c_double, c_int]
         L.tenom_advance_host.argtypes = [VP, VP, VP, P(c_double), c_double, c_double, c_int]
         L.tenom_face_dump.argtypes = [VP, VP, c_int, VP, VP]
+        L.tenom_positivity_limit.argtypes = [VP, VP, c_int, VP, VP]
         L.tenom_status_word.argtypes = [VP, P(c_int), c_int]
         L.tenom_last_error.argtypes = [VP]
         L.tenom_last_error.restype = ctypes.c_char_p
@@ -109,7 +111,7 @@ def lib():
         L.tenom_rhs_noalloc.restype = c_int
         for name in ("tenom_scheme_default", "tenom_create", "tenom_destroy", "tenom_init_state", "tenom_rhs",
                      "tenom_max_dt", "tenom_rk3_step", "tenom_advance", "tenom_advance_host", "tenom_face_dump",
-                     "tenom_status_word", "tenom_kernel_timing", "tenom_fp64_peak"):
+                     "tenom_positivity_limit", "tenom_status_word", "tenom_kernel_timing", "tenom_fp64_peak"):
             getattr(L, name).restype = c_int
         _lib = L
     return _lib
@@ -128,7 +130,7 @@ def make_grid(shape, dx, bc, gamma=1.4):
 
 
 def make_scheme(K=6, limiter=LIM_MP, ct_mode=None, ct_const=1e-5, mp_alpha=1.25, mp_beta=4.0, mp_curv=CURV_M4,
-                weights=W_TENOM, d=None, decisions=DECIDE_FILTERED):
+                weights=W_TENOM, d=None, decisions=DECIDE_FILTERED, positivity=PP_OFF):
     s = tenom_scheme()
     st = lib().tenom_scheme_default(ctypes.byref(s), K)
     if st != TENOM_OK:
@@ -142,6 +144,7 @@ def make_scheme(K=6, limiter=LIM_MP, ct_mode=None, ct_const=1e-5, mp_alpha=1.25,
     s.mp_curv = mp_curv
     s.weights = weights
     s.decisions = decisions
+    s.positivity = positivity
     if d is not None:
         for k in range(6):
             s.d[k] = d[k] if k < len(d) else 0.0
@@ -270,6 +273,13 @@ class Solver:
         self._check(lib().tenom_face_dump(self._ctx, _ptr(U), axis, _ptr(F), _ptr(fl) if fl is not None else None),
                     "tenom_face_dump")
         return F, fl
+
+    def positivity_limit(self, U, axis, dt_dev, F):
+        """The positivity limiter of a stage of length dt_dev applied in place to face
+        fluxes F (as face_dump returns them) of one axis at the state U."""
+        self._check(lib().tenom_positivity_limit(self._ctx, _ptr(U), axis, _ptr(dt_dev), _ptr(F)),
+                    "tenom_positivity_limit")
+        return F
 
     # ---- frozen-branch adjoint ----
     def flags_bytes(self):

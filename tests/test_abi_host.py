@@ -78,3 +78,14 @@ def test_null_context_calls_fail_cleanly(T):
     assert L.tenom_rhs(None, None, None) == T.TENOM_E_INVALID
     assert L.tenom_destroy(None) == T.TENOM_OK
     assert L.tenom_last_error(None) == b""
+
+
+def test_positivity_flag_validated_on_host(T):
+    """The positivity field takes TENOM_PP_OFF or TENOM_PP_ON; anything else is rejected."""
+    g = T.make_grid((16,), (0.1,), (0,))
+    s = T.make_scheme(6, positivity=T.PP_ON)
+    assert s.positivity == T.PP_ON and T.make_scheme(6).positivity == T.PP_OFF
+    s.positivity = 2
+    ctx = ctypes.c_void_p()
+    assert T.lib().tenom_create(ctypes.byref(ctx), ctypes.byref(g), ctypes.byref(s), None) == T.TENOM_E_INVALID
+    assert not ctx.value
