@@ -224,96 +224,125 @@ __device__ __forceinline__ double state_pressure(const double (&W)[NV], double g
   return gm1 * (W[NV - 1] - 0.5 * m2 / W[0]);
 }
 
-template <int NV>
+/* The limiter proper at one face (cells c0 | c1, face lin), rarely reached; it re-reads its
+   inputs (cached) rather than keeping the common path's values live. */
+template <int NV, int AXIS>
+__device__ __forceinline__ void limit_face(const PosArgs& A, long long c0, long long c1, long long lin, long long ncell,
+                                        long long nface, double mu) {
+  const double gm1 = A.gamma - 1.0;
+  double Us[2][NV], FH[NV], Fc[2][NV], sp[2];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    Us[0][v] = A.U[v * ncell + c0];
+    Us[1][v] = A.U[v * ncell + c1];
+    FH[v] = A.F[v * nface + lin];
+  }
+#pragma unroll
+  for (int sd = 0; sd < 2; ++sd) {
+    const double rho = Us[sd][0];
+    double vel[NV - 2], ke = 0.0;
+#pragma unroll
+    for (int d = 0; d < NV - 2; ++d) {
+      vel[d] = Us[sd][1 + d] / rho;
+      ke += Us[sd][1 + d] * vel[d];
+    }
+    const double p = gm1 * (Us[sd][NV - 1] - 0.5 * ke);
+    const double un = vel[AXIS];
+    Fc[sd][0] = Us[sd][1 + AXIS];
+#pragma unroll
+    for (int d = 0; d < NV - 2; ++d) Fc[sd][1 + d] = Us[sd][1 + d] * un + (d == AXIS ? p : 0.0);
+    Fc[sd][NV - 1] = (Us[sd][NV - 1] + p) * un;
+    sp[sd] = fabs(un) + sqrt(A.gamma * p / rho);
+  }
+  const double alpha = fmax(sp[0], sp[1]);
+  double FLF[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) FLF[v] = 0.5 * (Fc[0][v] + Fc[1][v] - alpha * (Us[1][v] - Us[0][v]));
+  /* density factor over both one-sided states (left loses F, right gains it) */
+  double th = 1.0;
+#pragma unroll
+  for (int sd = 0; sd < 2; ++sd) {
+    const double m = sd ? mu : -mu;
+    const double rlf = Us[sd][0] + m * FLF[0];
+    const double rh = Us[sd][0] + m * FH[0];
+    const double eps = fmin(1e-13, rlf);
+    if (rh < eps) th = fmin(th, (rlf - eps) / (rlf - rh));
+  }
+  double F1[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) F1[v] = (th == 1.0) ? FH[v] : FLF[v] + th * (FH[v] - FLF[v]);
+  /* pressure factor on the density-limited flux */
+  double tp = 1.0;
+#pragma unroll
+  for (int sd = 0; sd < 2; ++sd) {
+    const double m = sd ? mu : -mu;
+    double Wlf[NV], W1[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      Wlf[v] = Us[sd][v] + m * FLF[v];
+      W1[v] = Us[sd][v] + m * F1[v];
+    }
+    const double plf = state_pressure<NV>(Wlf, gm1), p1 = state_pressure<NV>(W1, gm1);
+    const double eps = fmin(1e-13, plf);
+    if (p1 < eps) tp = fmin(tp, (plf - eps) / (plf - p1));
+  }
+  if (th < 1.0 || tp < 1.0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) A.F[v * nface + lin] = (tp == 1.0) ? F1[v] : FLF[v] + tp * (F1[v] - FLF[v]);
+  }
+}
+
+template <int NV, int AXIS>
 __global__ void positivity_kernel(const PosArgs A) {
   const double dt = *A.dt;
   if (!(dt > 0.0)) return;  /* a step past t_end: nothing moves */
-  const int a = A.axis;
-  int fn[3] = {A.n[0], A.n[1], A.n[2]};
-  fn[a] += 1;
+  const int fn0 = A.n[0] + (AXIS == 0), fn1 = A.n[1] + (AXIS == 1), fn2 = A.n[2] + (AXIS == 2);
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= fn[0]) return;
+  if (x >= fn0) return;
   const long long ncell = (long long)A.n[0] * A.n[1] * A.n[2];
-  const long long nface = (long long)fn[0] * fn[1] * fn[2];
+  const long long nface = (long long)fn0 * fn1 * fn2;
   const double mu = A.mu_per_dt * dt;
   const double gm1 = A.gamma - 1.0;
-  const int na = A.n[a];
-  const long long cstride = (a == 0) ? 1 : (a == 1 ? (long long)A.n[0] : (long long)A.n[0] * A.n[1]);
-  for (int z = blockIdx.z; z < fn[2]; z += gridDim.z) {
-    for (int y = blockIdx.y; y < fn[1]; y += gridDim.y) {
-      const long long lin = x + (long long)fn[0] * (y + (long long)fn[1] * z);
-      int idx[3] = {x, y, z};
-      const int f = idx[a];
+  const int na = A.n[AXIS];
+  const bool periodic = A.bc[AXIS] == TENOM_BC_PERIODIC;
+  const long long cstride = (AXIS == 0) ? 1 : (AXIS == 1 ? (long long)A.n[0] : (long long)A.n[0] * A.n[1]);
+  for (int z = blockIdx.z; z < fn2; z += gridDim.z) {
+    for (int y = blockIdx.y; y < fn1; y += gridDim.y) {
+      const long long lin = x + (long long)fn0 * (y + (long long)fn1 * z);
+      const int f = (AXIS == 0) ? x : (AXIS == 1 ? y : z);
       int jl = f - 1, jr = f;
-      if (A.bc[a] == TENOM_BC_PERIODIC) {
+      if (periodic) {
         if (jl < 0) jl += na;
         if (jr >= na) jr -= na;
       } else {
         if (jl < 0) jl = 0;
         if (jr > na - 1) jr = na - 1;
       }
-      idx[a] = 0;
-      const long long base = idx[0] + (long long)A.n[0] * (idx[1] + (long long)A.n[1] * idx[2]);
-      const long long cell[2] = {base + jl * cstride, base + jr * cstride};
-      double Us[2][NV], Fc[2][NV], sp[2];
+      /* cell index of (x, y, z) with the AXIS coordinate set to 0 */
+      const long long base = (AXIS == 0 ? 0 : x) + (long long)A.n[0] * ((AXIS == 1 ? 0 : y) +
+                                                                       (long long)A.n[1] * (AXIS == 2 ? 0 : z));
+      const long long c0 = base + jl * cstride, c1 = base + jr * cstride;
+      /* early exit, division-free: when both one-sided states made with F^H have density
+         and pressure (tested as rho p against 2e-13 rho) at least 2e-13, twice the largest
+         floor, neither factor can fall below 1 and the face is left as it is */
+      double FH[NV], W0[NV], W1[NV];
 #pragma unroll
-      for (int sd = 0; sd < 2; ++sd) {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) Us[sd][v] = A.U[v * ncell + cell[sd]];
-        const double rho = Us[sd][0];
-        double vel[NV - 2], ke = 0.0;
-#pragma unroll
-        for (int d = 0; d < NV - 2; ++d) {
-          vel[d] = Us[sd][1 + d] / rho;
-          ke += Us[sd][1 + d] * vel[d];
-        }
-        const double p = gm1 * (Us[sd][NV - 1] - 0.5 * ke);
-        const double un = vel[a];
-        Fc[sd][0] = Us[sd][1 + a];
-#pragma unroll
-        for (int d = 0; d < NV - 2; ++d) Fc[sd][1 + d] = Us[sd][1 + d] * un + (d == a ? p : 0.0);
-        Fc[sd][NV - 1] = (Us[sd][NV - 1] + p) * un;
-        sp[sd] = fabs(un) + sqrt(A.gamma * p / rho);
-      }
-      const double alpha = fmax(sp[0], sp[1]);
-      double FLF[NV], FH[NV];
+      for (int v = 0; v < NV; ++v) FH[v] = A.F[v * nface + lin];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        FLF[v] = 0.5 * (Fc[0][v] + Fc[1][v] - alpha * (Us[1][v] - Us[0][v]));
-        FH[v] = A.F[v * nface + lin];
+        W0[v] = A.U[v * ncell + c0] - mu * FH[v];
+        W1[v] = A.U[v * ncell + c1] + mu * FH[v];
       }
-      /* density factor over both one-sided states (left loses F, right gains it) */
-      double th = 1.0;
+      double m0 = 0.0, m1 = 0.0;
 #pragma unroll
-      for (int sd = 0; sd < 2; ++sd) {
-        const double m = sd ? mu : -mu;
-        const double rlf = Us[sd][0] + m * FLF[0];
-        const double rh = Us[sd][0] + m * FH[0];
-        const double eps = fmin(1e-13, rlf);
-        if (rh < eps) th = fmin(th, (rlf - eps) / (rlf - rh));
+      for (int d = 1; d < NV - 1; ++d) {
+        m0 += W0[d] * W0[d];
+        m1 += W1[d] * W1[d];
       }
-      double F1[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) F1[v] = (th == 1.0) ? FH[v] : FLF[v] + th * (FH[v] - FLF[v]);
-      /* pressure factor on the density-limited flux */
-      double tp = 1.0;
-#pragma unroll
-      for (int sd = 0; sd < 2; ++sd) {
-        const double m = sd ? mu : -mu;
-        double Wlf[NV], W1[NV];
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          Wlf[v] = Us[sd][v] + m * FLF[v];
-          W1[v] = Us[sd][v] + m * F1[v];
-        }
-        const double plf = state_pressure<NV>(Wlf, gm1), p1 = state_pressure<NV>(W1, gm1);
-        const double eps = fmin(1e-13, plf);
-        if (p1 < eps) tp = fmin(tp, (plf - eps) / (plf - p1));
-      }
-      if (th < 1.0 || tp < 1.0) {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) A.F[v * nface + lin] = (tp == 1.0) ? F1[v] : FLF[v] + tp * (F1[v] - FLF[v]);
-      }
+      const bool quiet = (W0[0] >= 2e-13) && (W1[0] >= 2e-13) &&
+                         (gm1 * (W0[0] * W0[NV - 1] - 0.5 * m0) >= 2e-13 * W0[0]) &&
+                         (gm1 * (W1[0] * W1[NV - 1] - 0.5 * m1) >= 2e-13 * W1[0]);
+      if (!quiet) limit_face<NV, AXIS>(A, c0, c1, lin, ncell, nface, mu);
     }
   }
 }
@@ -323,9 +352,15 @@ static cudaError_t launch_positivity_kernel(int nv, const PosArgs& p, cudaStream
   fn[p.axis] += 1;
   const dim3 grid((unsigned)((fn[0] + 127) / 128), (unsigned)(fn[1] < 65535 ? fn[1] : 65535),
                   (unsigned)(fn[2] < 65535 ? fn[2] : 65535));
-  if (nv == 3) positivity_kernel<3><<<grid, 128, 0, st>>>(p);
-  else if (nv == 4) positivity_kernel<4><<<grid, 128, 0, st>>>(p);
-  else positivity_kernel<5><<<grid, 128, 0, st>>>(p);
+  if (nv == 3) positivity_kernel<3, 0><<<grid, 128, 0, st>>>(p);
+  else if (nv == 4) {
+    if (p.axis == 0) positivity_kernel<4, 0><<<grid, 128, 0, st>>>(p);
+    else positivity_kernel<4, 1><<<grid, 128, 0, st>>>(p);
+  } else {
+    if (p.axis == 0) positivity_kernel<5, 0><<<grid, 128, 0, st>>>(p);
+    else if (p.axis == 1) positivity_kernel<5, 1><<<grid, 128, 0, st>>>(p);
+    else positivity_kernel<5, 2><<<grid, 128, 0, st>>>(p);
+  }
   return cudaGetLastError();
 }
 
