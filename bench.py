@@ -305,7 +305,8 @@ def run_ours(args):
     name = args.workload
     gen, shape, K, lim = WORKLOADS[name]
     prim, dx = make_prim(name, args.seed + rank)
-    S = T.Solver(shape, dx, (T.BC_PERIODIC,) * len(shape), T.make_scheme(K, limiter=lim))
+    pp = T.PP_ON if args.positivity else T.PP_OFF
+    S = T.Solver(shape, dx, (T.BC_PERIODIC,) * len(shape), T.make_scheme(K, limiter=lim, positivity=pp))
     U0 = S.init_state(torch.from_numpy(prim).cuda())
     U = U0.clone()
     ncell = int(np.prod(shape))
@@ -376,7 +377,8 @@ def run_ours(args):
             "frac_fp64_issue": fpi * faces_per_launch / (face_ms * 1e-3) / (304 * mhz * 1e6) if face_ms > 0 else None,
             "note": "FP64 instructions the kernel executes (ncu, %s) at the live launch time over the "
                     "FP64 pipe's 304 lanes per clock" % fig["file"]}
-    launches_per_step = 3 + 3 * (len(shape) + 2)  # per stage: primitives, one sweep per axis, update; dt
+    # per stage: primitives, one sweep per axis (and one limiter pass per axis), update; dt
+    launches_per_step = 3 + 3 * (len(shape) * (2 if args.positivity else 1) + 2)
 
     out = {"metric": "cell-updates/s per RK stage (FP64)", "value": value, "unit": "cell-updates/s",
            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -384,6 +386,7 @@ def run_ours(args):
            "data": "synthetic (seeded, shaped like the paper's workloads)",
            "config": {"workload": name, "shape": list(shape), "K": K, "limiter": "MP" if lim == 0 else "TVD5",
                       "parallelism": "replicas" if ws > 1 else "single", "cfl": 0.4,
+                      "positivity_limiter": bool(args.positivity),
                       "l2": "working set per stage (state, stage buffer, face buffers: %.0f MB) > L2"
                             % ((2 * S.nv * ncell + S.nv * nface) * 8 / 1e6)},
            "e2e": {"value": e2e, "unit": "cell-updates/s", "h2d_bytes_per_step": state_bytes,
@@ -843,6 +846,8 @@ def main():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--ref-seconds", type=float, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--positivity", action="store_true",
+                    help="grid workloads: add the positivity-preserving flux limiter to every RK stage")
     ap.add_argument("--tape", default="auto", choices=["auto", "linear", "flags"],
                     help="adjoint workloads: tape of the recomputed segments")
     ap.add_argument("--rollout-steps", type=int, default=0,
