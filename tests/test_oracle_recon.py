@@ -209,6 +209,23 @@ def test_discontinuity_marks_nonsmooth(orc, K, lim):
     assert -1e-12 <= fh[0] <= 1.0 + 1e-12
 
 
+@pytest.mark.parametrize("K", [6, 8])
+@pytest.mark.parametrize("a,b,J", [(1.0, 1.0, 100.0), (-3.0, 0.25, -50.0), (10.0, -2.0, 1e3)])
+def test_renormalised_weights_reproduce_the_smooth_side(orc, K, a, b, J):
+    """Classical TENO weights (Eq. weight_renormalize): linear data a + b m with a jump J
+    between i+1 and i+2.  Exactly the candidates upwind of the jump (S0, S2 and, for K = 8,
+    S4) are smooth; each reproduces linear data exactly, so the renormalised combination
+    sum_{smooth} d_k f_k / sum_{smooth} d_k is the linear value at x_{i+1/2}, a + b/2,
+    whatever the jump (a dropped denominator or a wrong candidate set misses it)."""
+    S = orc.make_scheme(K, weights=orc.W_TENO)
+    ms = np.arange(-K // 2 + 1, K // 2 + 1)
+    v = a + b * ms + np.where(ms >= 2, J, 0.0)
+    fh, bits, _, _, _ = orc.recon(S, v[None, :])
+    smooth = (1 << 0) | (1 << 2) | ((1 << 4) if K == 8 else 0)
+    assert bits[0] == smooth
+    assert abs(fh[0] - (a + 0.5 * b)) <= 1e-13 * (abs(a) + abs(b))
+
+
 def test_cutoff_tie_is_smooth(orc):
     """Eq. cut-off: delta_k = 0 only for chi_k < C_T; with C_T = 0 every stencil is
     smooth, with C_T = 2 every stencil is nonsmooth (chi_k <= 1)."""
