@@ -282,6 +282,21 @@ def tvd5_paper(f):
     return f0 + 0.5 * phi * dm
 
 
+@pytest.mark.parametrize("curv,beta,fmax", [("M4", 4.0, 2.25), ("MM", 4.0, 1.5 + 4.0 / 3.0),
+                                             ("MM", 3.0, 2.5), ("MM", 1.0, 2.25)])
+def test_mp_bounds_curvature_variants_worked_example(orc, curv, beta, fmax):
+    """Hand-worked sequence f = (0, 0, 1, 10, 27, 27) for the curvature variants of
+    Section 4 (d^{MM}_{i+1/2} = minmod(d_i, d_{i+1})) and beta of Eq. large_curvature:
+    d_{i-1} = 1, d_i = 8, d_{i+1} = 8; d_{i+1/2} = 8 under both measures, d_{i-1/2} =
+    minmod4(-4, 31, 1, 8) = 0 under M4 but minmod(1, 8) = 1 under MM.  f^{UL} = 2.25,
+    f^{MD} = 5.5 - 4 = 1.5, f^{LC} = 1.5 + (beta/3) d_{i-1/2}; f^{L,min} = 1 and
+    f^{L,max} = min(10, max(2.25, f^{LC}))."""
+    S = orc.make_scheme(6, mp_curv=orc.CURV_M4 if curv == "M4" else orc.CURV_MM, mp_beta=beta)
+    p = orc.recon_parts(S, np.array([0.0, 0.0, 1.0, 10.0, 27.0, 27.0]))
+    assert p["mpmin"] == pytest.approx(1.0, abs=1e-15)
+    assert p["mpmax"] == pytest.approx(fmax, rel=1e-15)
+
+
 def test_tvd5_difference_form_matches_printed_formula(orc):
     S = orc.make_scheme(6, limiter=1)
     rng = np.random.default_rng(31)
