@@ -188,7 +188,8 @@ def cached_prim(name, seed):
 def oracle_rate(name, seconds=12.0, seed=2):
     """CPU oracle (single thread): one operator evaluation (all axes) on a row block of the
     workload's initial state, sized for about `seconds` of work.
-    Returns (cell-updates/s per stage, sample description, elapsed s)."""
+    Returns (cell-updates/s per stage, sample description, elapsed s); the block's row count
+    is left in oracle_rate.rows."""
     import numpy as np
     import oracle as orc
     gen, shape, K, lim = WORKLOADS[name]
@@ -215,7 +216,48 @@ def oracle_rate(name, seconds=12.0, seed=2):
     el = time.perf_counter() - t0
     sample = ("one operator evaluation (all %d axes, periodic wrap of the block) on a %s block of the "
               "%s initial state, 1 thread" % (len(shape), "x".join(str(n) for n in (shape[:-1] + (rows,))), name))
+    oracle_rate.rows = rows
     return nc / el, sample, el
+
+
+def _oracle_block_worker(job):
+    """One process of the all-cores oracle figure: one operator evaluation on its own block."""
+    import numpy as np
+    import oracle as orc
+    sh, dx, bc, K, lim, p = job
+    g = orc.make_grid(sh, dx, bc)
+    S = orc.make_scheme(K, limiter=lim)
+    U = orc.init_state(g, p)
+    t0 = time.perf_counter()
+    orc.rhs(g, S, U)
+    return int(np.prod(sh)), time.perf_counter() - t0
+
+
+def oracle_rate_all_cores(name, rows_single, seed=2):
+    """CPU oracle on every core the process may use: the same single-thread code, one process
+    per core (spawned), each evaluating the operator on its own block of rows_single rows of
+    the workload's initial state (wrapping around the grid).  Returns (cell-updates/s per
+    stage = all cells / the slowest process's time, cores, sample)."""
+    import multiprocessing as mp
+    import numpy as np
+    import oracle as orc
+    orc.build()
+    gen, shape, K, lim = WORKLOADS[name]
+    prim, dx = cached_prim(name, seed)
+    ncores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    jobs = []
+    for w in range(ncores):
+        idx = (np.arange(rows_single) + w * rows_single) % prim.shape[1]
+        p = np.ascontiguousarray(np.take(prim, idx, axis=1))
+        sh = tuple(shape[:-1]) + (rows_single,)
+        jobs.append((sh, dx, (orc.BC_PERIODIC,) * len(shape), K, lim, p))
+    with mp.get_context("spawn").Pool(ncores) as pool:
+        res = pool.map(_oracle_block_worker, jobs, chunksize=1)
+    cells = sum(c for c, _ in res)
+    el = max(t for _, t in res)
+    sample = ("%d processes, each one operator evaluation on its own %s block of the %s initial state"
+              % (ncores, "x".join(str(n) for n in (shape[:-1] + (rows_single,))), name))
+    return cells / el, ncores, sample
 
 
 def oracle_rate_batch(name, seconds):
@@ -395,7 +437,10 @@ def run_ours(args):
            "roofline": roof, "clocks": clk}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         r, sample, el = oracle_rate(name, seconds=args.ref_seconds or 12.0, seed=args.seed)
-        out["cpu_baseline"] = {"value": r, "unit": "cell-updates/s", "cores": 1, "kind": "oracle", "sample": sample}
+        ra, cores, sample_all = oracle_rate_all_cores(name, oracle_rate.rows, seed=args.seed)
+        out["cpu_baseline"] = {"value": ra, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+                               "sample": sample_all,
+                               "single_thread": {"value": r, "cores": 1, "sample": sample}}
     if rank == 0:
         print(json.dumps(out), flush=True)
     S.close()
