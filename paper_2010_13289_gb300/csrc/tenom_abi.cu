@@ -292,6 +292,37 @@ __device__ __forceinline__ void limit_face(const PosArgs& A, long long c0, long 
   }
 }
 
+/* Proof in FP32 that the one-sided state W = U + m F (m = -+mu, F the high-order flux) has
+   density >= 2e-13 and rho p / (gamma - 1) = rho E - |m|^2/2 >= 2e-13 rho / (gamma - 1),
+   i.e. p >= 2e-13.  Inputs are truncated to FP32 on the integer pipe (relative error
+   < 2^-23; below the FP32 normal range, absolute error < 1.2e-38; NaN and overflow become
+   infinities, which fail every test).  With M_v = |u_v| + |m f_v| + 1e-30, each FP32 w_v
+   is within 3.1e-7 M_v of the exact W_v, and the FP32 pressure form within 5e-7 B of the
+   exact one, B the sum of the magnitudes it is built from (below); demanding 1e-5 M_0 and
+   1e-5 B of headroom (20 times those bounds) makes a true result a proof.  False means
+   "not proven", not "fails". */
+template <int NV>
+__device__ __forceinline__ bool screen_fp32(const double (&U)[NV], const double (&F)[NV], float m, float gm1f) {
+  float w[NV], M[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    const float a = f32_rz(U[v]), f = f32_rz(F[v]);
+    w[v] = fmaf(m, f, a);
+    M[v] = fabsf(a) + fabsf(m * f) + 1e-30f;
+  }
+  float m2 = 0.0f, Bm = 0.0f;
+#pragma unroll
+  for (int d = 1; d < NV - 1; ++d) {
+    m2 = fmaf(w[d], w[d], m2);
+    Bm = fmaf(M[d], fabsf(w[d]) + M[d], Bm);
+  }
+  const float pe = w[0] * w[NV - 1];
+  const float rp = gm1f * (pe - 0.5f * m2);
+  const float B = gm1f * (M[0] * (fabsf(w[NV - 1]) + M[NV - 1]) + M[NV - 1] * (fabsf(w[0]) + M[0]) + Bm +
+                          fabsf(pe) + 0.5f * m2);
+  return (w[0] - 1e-5f * M[0] >= 2.0001e-13f) && (rp - 1e-5f * B >= 2.0001e-13f * (w[0] + 1e-5f * M[0]));
+}
+
 template <int NV, int AXIS>
 __global__ void positivity_kernel(const PosArgs A) {
   const double dt = *A.dt;
@@ -303,6 +334,7 @@ __global__ void positivity_kernel(const PosArgs A) {
   const long long nface = (long long)fn0 * fn1 * fn2;
   const double mu = A.mu_per_dt * dt;
   const double gm1 = A.gamma - 1.0;
+  const float muf = f32_rz(mu), gm1f = f32_rz(gm1);
   const int na = A.n[AXIS];
   const bool periodic = A.bc[AXIS] == TENOM_BC_PERIODIC;
   const long long cstride = (AXIS == 0) ? 1 : (AXIS == 1 ? (long long)A.n[0] : (long long)A.n[0] * A.n[1]);
@@ -322,16 +354,23 @@ __global__ void positivity_kernel(const PosArgs A) {
       const long long base = (AXIS == 0 ? 0 : x) + (long long)A.n[0] * ((AXIS == 1 ? 0 : y) +
                                                                        (long long)A.n[1] * (AXIS == 2 ? 0 : z));
       const long long c0 = base + jl * cstride, c1 = base + jr * cstride;
-      /* early exit, division-free: when both one-sided states made with F^H have density
-         and pressure (tested as rho p against 2e-13 rho) at least 2e-13, twice the largest
-         floor, neither factor can fall below 1 and the face is left as it is */
-      double FH[NV], W0[NV], W1[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) FH[v] = A.F[v * nface + lin];
+      /* early exit: when both one-sided states made with F^H have density and pressure
+         (tested as rho p against 2e-13 rho, division-free) at least 2e-13, twice the largest
+         floor, neither factor can fall below 1 and the face is left as it is.  First proven
+         in FP32 (screen_fp32), else tested in FP64. */
+      double FH[NV], Ua[NV], Ub[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        W0[v] = A.U[v * ncell + c0] - mu * FH[v];
-        W1[v] = A.U[v * ncell + c1] + mu * FH[v];
+        FH[v] = A.F[v * nface + lin];
+        Ua[v] = A.U[v * ncell + c0];
+        Ub[v] = A.U[v * ncell + c1];
+      }
+      if (screen_fp32<NV>(Ua, FH, -muf, gm1f) && screen_fp32<NV>(Ub, FH, muf, gm1f)) continue;
+      double W0[NV], W1[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        W0[v] = Ua[v] - mu * FH[v];
+        W1[v] = Ub[v] + mu * FH[v];
       }
       double m0 = 0.0, m1 = 0.0;
 #pragma unroll
