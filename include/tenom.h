@@ -87,10 +87,10 @@ typedef struct tenom_scheme {
   int positivity;   /* TENOM_PP_OFF (default) or TENOM_PP_ON: the positivity-preserving flux
                        limiter that Section 4.4 applies (Hu, Adams & Shu 2013).  It belongs to a
                        forward-Euler stage of length dt, so it acts in the stepping calls
-                       (tenom_rk3_step, tenom_advance, tenom_advance_host: in every SSP-RK3
-                       stage, with that step's dt); tenom_rhs, tenom_rhs_noalloc and
-                       tenom_face_dump return the unlimited operator; the adjoint calls return
-                       TENOM_E_UNSUPPORTED and tenom_batch_create rejects it.  Per face of axis
+                       (tenom_rk3_step, tenom_advance, tenom_advance_host and the batched
+                       steps: in every SSP-RK3 stage, with that step's dt); tenom_rhs,
+                       tenom_rhs_noalloc and tenom_face_dump return the unlimited operator;
+                       the adjoint calls return TENOM_E_UNSUPPORTED.  Per face of axis
                        a the high-order flux F^H is pulled towards the local Lax-Friedrichs flux
                        F^LF = (F(U_L) + F(U_R) - alpha (U_R - U_L))/2, alpha = max(|u_a| + c) of
                        the two cells: F = F^LF + theta (F^H - F^LF), theta in [0, 1] the product

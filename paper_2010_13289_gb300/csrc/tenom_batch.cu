@@ -21,86 +21,9 @@
 
 #include "tenom.h"
 #include "tenom_internal.h"
+#include "tenom_batch_kernel.cuh"
 
 namespace tenom {
-
-struct BatchArgs {
-  const int* n;
-  const long long* off;
-  const double* dx;
-  const int* bc;
-  const double* dt;
-  const int2* items;
-  int nitems;
-  int* counter;
-  int* status;
-  long long total;
-  double gamma;
-  SchemeDev sch;
-};
-
-template <int K, int TILE>
-struct BatchTile {
-  static constexpr int NV = 3;
-  static constexpr int NP = TILE + K - 1;
-  static constexpr size_t SMEM = sizeof(double) * (PointLayout<3>::NC * NP + NV * TILE);
-};
-
-/* stage: 1 -> out = Us + dt L(Us); 2,3 -> out = cA U0 + cB (Us + dt L(Us)) */
-template <int K, int LIM, int TILE>
-__global__ void __launch_bounds__(TILE)
-batch_stage_kernel(const BatchArgs A, const double* __restrict__ Us, const double* __restrict__ U0, double* out,
-                   int mode, double cA, double cB) {
-  using T = BatchTile<K, TILE>;
-  constexpr int NV = 3, H = K / 2, NP = T::NP;
-  extern __shared__ double sm[];
-  double* Fs = sm + PointLayout<3>::NC * NP;
-  __shared__ int s_item;
-  const int tid = threadIdx.x;
-  int st = 0;
-  for (;;) {
-    if (tid == 0) s_item = atomicAdd(A.counter, 1);
-    __syncthreads();
-    const int it = s_item;
-    __syncthreads();
-    if (it >= A.nitems) break;
-    const int2 w = A.items[it];
-    const int j = w.x, f0 = w.y;
-    const double dt = A.dt[j];
-    if (dt == 0.0) continue;  /* finished problem (uniform across the CTA) */
-    const int n = A.n[j];
-    const long long off = A.off[j];
-    const int bc = A.bc[j];
-    for (int p = tid; p < NP; p += TILE) {
-      const int jj = bc_wrap(f0 - H + p, n, bc);
-      double u[NV];
-#pragma unroll
-      for (int q = 0; q < NV; ++q) u[q] = Us[q * A.total + off + jj];
-      stage_point<NV, 0>(u, A.gamma, sm, NP, p, st);
-    }
-    __syncthreads();
-    if (f0 + tid <= n) {
-      double Fh[NV];
-      face_flux_smem<NV, K, LIM, 0, 1>(sm, NP, tid, 0, A.gamma, A.sch, Fh, nullptr, st);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) Fs[v * TILE + tid] = Fh[v];
-    }
-    __syncthreads();
-    const int c = f0 + tid;
-    if (tid < TILE - 1 && c < n) {
-      const double dxj = A.dx[j];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        const double r = 0.0 - (Fs[v * TILE + tid + 1] - Fs[v * TILE + tid]) / dxj;
-        const long long g = v * A.total + off + c;
-        const double t1 = Us[g] + dt * r;
-        out[g] = (mode == 1) ? t1 : cA * U0[g] + cB * t1;
-      }
-    }
-    __syncthreads();
-  }
-  if (st) atomicOr(A.status, st);
-}
 
 /* per-problem max_i (|u| + c)_i / dx over cell tiles (problem, first cell) of 256 cells */
 __global__ void batch_signal_kernel(const double* __restrict__ U, long long total, const int2* citems, const int* n,
@@ -169,12 +92,11 @@ __global__ void batch_init_kernel(const double* prim, double* U, long long total
   }
 }
 
-using StageFn = void (*)(const BatchArgs, const double*, const double*, double*, int, double, double);
-
 template <int K, int LIM, int TILE>
-static StageFn stage_fn() { return batch_stage_kernel<K, LIM, TILE>; }
+static StageFn stage_fn() { return batch_stage_kernel<K, LIM, TILE, false>; }
 
-static StageFn pick_stage(int K, int lim, int tile) {
+static StageFn pick_stage(int K, int lim, int tile, bool pp) {
+  if (pp) return pick_stage_pp(K, lim, tile);
 #define TENOM_PICK(KK, LL, TT) if (K == KK && lim == LL && tile == TT) return stage_fn<KK, LL, TT>();
   TENOM_PICK(6, LIM_MP, 64) TENOM_PICK(6, LIM_MP, 128) TENOM_PICK(6, LIM_MP, 256)
   TENOM_PICK(6, LIM_TVD5, 64) TENOM_PICK(6, LIM_TVD5, 128) TENOM_PICK(6, LIM_TVD5, 256)
@@ -251,7 +173,7 @@ static cudaError_t build_items(tenom_batch* b, int tile) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
   b->tile = tile;
   /* shared-memory size of the stage kernel for this tile (set outside any graph capture) */
-  StageFn fn = pick_stage(b->s.K, b->s.limiter, tile);
+  StageFn fn = pick_stage(b->s.K, b->s.limiter, tile, b->s.positivity == TENOM_PP_ON);
   if (e == cudaSuccess && fn)
     e = cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)stage_smem(b->s.K, tile));
@@ -277,7 +199,7 @@ static BatchArgs batch_args(tenom_batch* b, int stage) {
 }
 
 static cudaError_t launch_stage_b(tenom_batch* b, int stage, double* U, cudaStream_t st) {
-  StageFn fn = pick_stage(b->s.K, b->s.limiter, b->tile);
+  StageFn fn = pick_stage(b->s.K, b->s.limiter, b->tile, b->s.positivity == TENOM_PP_ON);
   if (!fn) return cudaErrorNotSupported;
   const size_t smem = stage_smem(b->s.K, b->tile);
   BatchArgs a = batch_args(b, stage);
@@ -321,7 +243,8 @@ tenom_status tenom_batch_create(tenom_batch** out, int nprob, const int* n, cons
   if (scheme->K != 6 && scheme->K != 8) return bfail(nullptr, TENOM_E_INVALID, "K must be 6 or 8");
   if (scheme->limiter != TENOM_LIM_MP && scheme->limiter != TENOM_LIM_TVD5)
     return bfail(nullptr, TENOM_E_UNSUPPORTED, "limiter not built");
-  if (scheme->positivity != TENOM_PP_OFF) return bfail(nullptr, TENOM_E_UNSUPPORTED, "positivity limiter not built");
+  if (scheme->positivity != TENOM_PP_OFF && scheme->positivity != TENOM_PP_ON)
+    return bfail(nullptr, TENOM_E_INVALID, "bad positivity flag");
   tenom_batch* b = new tenom_batch();
   b->P = nprob;
   b->s = *scheme;
@@ -508,7 +431,7 @@ tenom_status tenom_batch_autotune(tenom_batch* b, double* U, int* tile_out, int*
   int bt = b->tile, bc = b->ctas_per_sm;
   for (int ti = 0; ti < 3 && e == cudaSuccess; ++ti) {
     e = build_items(b, tiles[ti]);
-    StageFn fn = pick_stage(b->s.K, b->s.limiter, tiles[ti]);
+    StageFn fn = pick_stage(b->s.K, b->s.limiter, tiles[ti], b->s.positivity == TENOM_PP_ON);
     int occ = 0;
     const size_t smem = stage_smem(b->s.K, tiles[ti]);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void*)fn, tiles[ti], smem);

@@ -1,4 +1,4 @@
-"""The positivity kernel's FP32 early-exit screen (screen_fp32 in csrc/tenom_abi.cu) claims a
+"""The positivity kernel's FP32 early-exit screen (screen_fp32 in csrc/tenom_positivity.cuh) claims a
 proof: when it returns true, the exact one-sided state W = U + m F has density >= 2e-13 and
 pressure >= 2e-13.  Its error bound is restated here in numpy float32 with the kernel's
 operations (truncating FP64 -> FP32 conversion, fused multiply-adds, the 1e-5 headroom) and
