@@ -712,7 +712,9 @@ def run_le_blanc(args):
     TENO8-MP with the minmod curvature and beta = 1 and the positivity-preserving flux
     limiter (Section 4.4), CFL 0.4, to t = 6, timed end to end on the device (a 900-cell
     grid is launch-bound: about 16 launches per step).  Also times the limiter's cost on the
-    2D 2048^2 broadband workload: step time with the limiter over step time without."""
+    2D 2048^2 broadband workload (step time with the limiter over step time without) and
+    512 Le Blanc problems of log-uniform size 128..8192 through the batched launch, with and
+    without the limiter."""
     import numpy as np
     import torch
     torch.cuda.set_device(0)
@@ -768,6 +770,30 @@ def run_le_blanc(args):
         torch.cuda.synchronize()
         ms2[label] = e0.elapsed_time(e1) / args.steps
         S2.close()
+    # batched: 512 Le Blanc problems of log-uniform size 128..8192 (each on its own [0, 9]
+    # grid), one persistent launch per RK stage, with and without the limiter
+    sizes = PB.batch_sizes(512, 4, 128, 8192)
+    bprims = [PB.le_blanc_1d(int(m)) for m in sizes]
+    bat = {}
+    for label, pp in (("off", T.PP_OFF), ("on", T.PP_ON)):
+        B = T.Batch(sizes, np.array([d for _, d in bprims]), gamma=gam,
+                    scheme=T.make_scheme(8, limiter=T.LIM_MP, mp_curv=T.CURV_MM, mp_beta=1.0, positivity=pp))
+        bp = np.zeros((3, B.total))
+        for j in range(B.P):
+            bp[:, B.off[j]:B.off[j + 1]] = bprims[j][0]
+        UB = B.init_state(torch.from_numpy(bp).cuda())
+        tile, ctas = B.autotune(UB)
+        B.step(UB, nsteps=args.warmup)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        B.step(UB, nsteps=args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bms = e0.elapsed_time(e1) / args.steps
+        bat[label] = {"ms_per_step": bms, "cell_updates_per_s": float(B.total) * 3 / (bms * 1e-3),
+                      "tile": tile, "ctas_per_sm": ctas}
+        B.close()
     clk = clocks.stop()
     ms = statistics.median(runs)
     out = {"metric": "cell-updates/s per RK stage (FP64)", "value": float(n) * 3 * steps / (ms * 1e-3),
@@ -781,6 +807,9 @@ def run_le_blanc(args):
                            "finite": bool(np.isfinite(Un).all()), "status_word": int(st)},
            "limiter_cost_2d_2048_teno6_mp": {"ms_per_step_off": ms2["off"], "ms_per_step_on": ms2["on"],
                                              "ratio": ms2["on"] / ms2["off"]},
+           "batched_512_le_blanc": {"cells": int(np.sum(sizes)), "steps": args.steps, "limiter_on": bat["on"],
+                                    "limiter_off": bat["off"],
+                                    "limiter_cost": bat["on"]["ms_per_step"] / bat["off"]["ms_per_step"]},
            "clocks": clk}
     print(json.dumps(out), flush=True)
 
