@@ -285,6 +285,13 @@ def oracle_rate_batch(name, seconds):
         used, nprob, cells), el
 
 
+def launches_per_step(dim, positivity):
+    """Kernel launches of one SSP-RK3 step of a grid workload: the signal-speed reduction, dt
+    and the time update, and per stage the primitives, one face sweep per axis (plus one
+    limiter pass per axis when the positivity limiter is on) and the cell update."""
+    return 3 + 3 * (dim * (2 if positivity else 1) + 2)
+
+
 def grid_config(name, ws, positivity):
     """The config object of a grid workload, identical in both arms."""
     gen, shape, K, lim = WORKLOADS[name]
@@ -445,8 +452,7 @@ def run_ours(args):
             "frac_fp64_issue": fpi * faces_per_launch / (face_ms * 1e-3) / (304 * mhz * 1e6) if face_ms > 0 else None,
             "note": "FP64 instructions the kernel executes (ncu, %s) at the live launch time over the "
                     "FP64 pipe's 304 lanes per clock" % fig["file"]}
-    # per stage: primitives, one sweep per axis (and one limiter pass per axis), update; dt
-    launches_per_step = 3 + 3 * (len(shape) * (2 if args.positivity else 1) + 2)
+    lps = launches_per_step(len(shape), args.positivity)
 
     out = {"metric": "cell-updates/s per RK stage (FP64)", "value": value, "unit": "cell-updates/s",
            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -455,7 +461,7 @@ def run_ours(args):
            "config": grid_config(name, ws, args.positivity),
            "e2e": {"value": e2e, "unit": "cell-updates/s", "h2d_bytes_per_step": state_bytes,
                    "d2h_bytes_per_step": state_bytes},
-           "gpu_launches": launches_per_step * args.steps,
+           "gpu_launches": lps * args.steps,
            "roofline": roof, "clocks": clk}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         r, sample, el = oracle_rate(name, seconds=args.ref_seconds or 12.0, seed=args.seed)
