@@ -89,3 +89,16 @@ def test_positivity_flag_validated_on_host(T):
     ctx = ctypes.c_void_p()
     assert T.lib().tenom_create(ctypes.byref(ctx), ctypes.byref(g), ctypes.byref(s), None) == T.TENOM_E_INVALID
     assert not ctx.value
+
+
+def test_batch_create_validates_positivity_on_host(T):
+    """tenom_batch_create rejects a positivity flag other than off/on before any CUDA call."""
+    import numpy as np
+    n = np.array([64, 80], dtype=np.int32)
+    dx = np.array([0.01, 0.01])
+    s = T.make_scheme(6)
+    s.positivity = 7
+    b = ctypes.c_void_p()
+    st = T.lib().tenom_batch_create(ctypes.byref(b), 2, ctypes.c_void_p(n.ctypes.data),
+                                    ctypes.c_void_p(dx.ctypes.data), None, 1.4, ctypes.byref(s), None)
+    assert st == T.TENOM_E_INVALID and not b.value
