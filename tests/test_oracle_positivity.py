@@ -41,11 +41,12 @@ def face_neighbours(U, a, n, periodic):
     return np.take(U, left, axis=ax), np.take(U, right, axis=ax)
 
 
-def evolved_states(orc, shape, seed, steps):
+def evolved_states(orc, shape, seed, steps, bc=None):
     """Seeded near-vacuum state advanced `steps` limited SSP-RK3 steps (CFL 0.4): states
     on which the limiter is active."""
     D = len(shape)
-    g = orc.make_grid(tuple(reversed(shape)), (0.1,) * D, (orc.BC_PERIODIC,) * D, gamma=1.4)
+    bc = orc.BC_PERIODIC if bc is None else bc
+    g = orc.make_grid(tuple(reversed(shape)), (0.1,) * D, (bc,) * D, gamma=1.4)
     s = orc.make_scheme(6, orc.LIM_MP, positivity=1)
     U = orc.init_state(g, PB.near_vacuum(shape, seed))
     out = []
@@ -56,20 +57,22 @@ def evolved_states(orc, shape, seed, steps):
     return g, s, out
 
 
-@pytest.mark.parametrize("shape,seed", [((128,), 1), ((24, 20), 0), ((10, 12, 8), 2)])
-def test_limited_flux_on_segment_and_one_sided_states_admissible(orc, shape, seed):
+@pytest.mark.parametrize("shape,seed,periodic", [((128,), 1, True), ((24, 20), 0, True), ((10, 12, 8), 2, True),
+                                                  ((128,), 3, False), ((24, 20), 4, False)])
+def test_limited_flux_on_segment_and_one_sided_states_admissible(orc, shape, seed, periodic):
     """Per face: F = F^LF + theta (F^H - F^LF) with one theta in [0, 1]; the one-sided
     states U_L - mu F and U_R + mu F (mu = 2 D dt/dx) keep density and pressure at or above
-    min(1e-13, the value with F^LF); theta < 1 only where F^H itself breaks that floor."""
+    min(1e-13, the value with F^LF); theta < 1 only where F^H itself breaks that floor.
+    On transmissive grids the cell outside a boundary face is the edge cell's copy."""
     D = len(shape)
-    g, s, states = evolved_states(orc, shape, seed, 6)
+    g, s, states = evolved_states(orc, shape, seed, 6, None if periodic else orc.BC_TRANSMISSIVE)
     nlim = 0
     for U, dt in states:
         for a in range(D):
             n = shape[D - 1 - a]
             FH = orc.faces(g, s, U, a)[0]
             F, _ = orc.faces_limited(g, s, U, a, dt)
-            UL, UR = face_neighbours(U, a, n, True)
+            UL, UR = face_neighbours(U, a, n, periodic)
             FLl, sl = euler_flux(UL, a, g.gamma)
             FLr, sr = euler_flux(UR, a, g.gamma)
             FLF = 0.5 * (FLl + FLr - np.maximum(sl, sr) * (UR - UL))
