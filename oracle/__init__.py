@@ -88,10 +88,15 @@ _lib = None
 
 
 def lib():
+    """The oracle library.  TENOM_ORACLE_LIB, when set, names a prebuilt copy to load instead
+    (the mutation tests load copies of the oracle with one mistake planted in them)."""
     global _lib
     if _lib is None:
-        build()
-        L = ctypes.CDLL(LIB_PATH)
+        path = os.environ.get("TENOM_ORACLE_LIB")
+        if not path:
+            build()
+            path = LIB_PATH
+        L = ctypes.CDLL(path)
         P = ctypes.POINTER
         dp, ip, u8p = P(ctypes.c_double), P(ctypes.c_int), P(ctypes.c_uint8)
         gp, sp = P(Grid), P(Scheme)

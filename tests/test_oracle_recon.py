@@ -356,6 +356,55 @@ def test_adaptive_ct_range_and_smooth_limit(orc):
     assert np.all((bct >= 7.0 - 1e-12) & (bct <= 10.5 + 1e-12))
 
 
+def adaptive_ct_examples():
+    """Rows of tests/golden/teno8a_cutoff_examples.txt: (f[8], eta window[4], eta_{i+1/2}, m, g,
+    beta, [beta])."""
+    out = []
+    for r in read_golden("teno8a_cutoff_examples.txt"):
+        x = [float(v) for v in r]
+        out.append((np.array(x[0:8]), x[8:12], x[12], x[13], x[14], x[15], int(x[16])))
+    return out
+
+
+def test_adaptive_ct_worked_examples(orc):
+    """TENO8A's adaptive cutoff between its limits (Section 2.4, Eqs. shock_indicator and
+    cut-off_adjust), on sequences worked out by hand from the printed formulas with
+    xi = 1e-3, C_r = 0.23, alpha_1 = 10.5, alpha_2 = 3.5 and
+    epsilon = 0.9 C_r / (1 - 0.9 C_r) xi^2 = 207/793000000 ~ 2.6103e-7.
+
+    First example, f_{i-3..i+4} = (0, 29, 30, 48, 64, 82, 90, 130) x 1e-4:
+      differences Delta f_{i-5/2 .. i+7/2} = (29, 1, 18, 16, 18, 8, 40) x 1e-4;
+      eta_{i-1} = (2*1*18e-8 + eps) / ((1 + 324)e-8 + eps) = 49248/278425 = 0.17688067,
+      eta_i = eta_{i+1} = (2*18*16e-8 + eps) / ((324 + 256)e-8 + eps) = 0.99340047,
+      eta_{i+2} = (2*18*8e-8 + eps) / ((324 + 64)e-8 + eps) = 0.75851442;
+      eta_{i+1/2} = min = 0.17688067 (below C_r, so m > 0),
+      m = 1 - 0.17688067 / 0.23 = 0.23095362,
+      g = (1 - m)^4 (1 + 4m) = 0.34979855 * 1.92381447 = 0.67293532,
+      beta = 10.5 - 3.5 (1 - 0.67293532) = 9.35527361, [beta] = 9, C_T = 1e-9.
+    The points just outside the window have eta_{i-2} = 0.0969 and eta_{i+3} = 0.394, so
+    a window shifted by one gives another eta_{i+1/2} ([beta] 7 or 10); epsilon with xi
+    in place of xi^2 makes every eta ~1 ([beta] = 10); (1 - m)^3 in g gives [beta] = 10.
+    The second row of the golden file lands on [beta] = 8 the same way.  The oracle must
+    reproduce beta to rounding and [beta] exactly."""
+    S = orc.make_scheme(8)
+    ex = adaptive_ct_examples()
+    assert len(ex) == 2
+    for f, etas, eh, m, g, beta, ib in ex:
+        # the golden rows are consistent with themselves: the chain of printed formulas
+        assert eh == pytest.approx(min(etas), rel=1e-13)
+        assert m == pytest.approx(1.0 - eh / 0.23, rel=1e-13)
+        assert g == pytest.approx((1 - m) ** 4 * (1 + 4 * m), rel=1e-13)
+        assert beta == pytest.approx(10.5 - 3.5 * (1 - g), rel=1e-14)
+        assert ib == int(np.floor(beta)) and ib in (8, 9)
+        _, _, cte, _, bct = orc.recon(S, f[None, :])
+        assert cte[0] == ib
+        assert bct[0] == pytest.approx(beta, rel=1e-13, abs=0)
+        # the f- side reconstructs the sequence mirrored about x_{i+1/2} (f'_m = f_{1-m});
+        # its eta'_j is eta_{1-j}, so its window {eta'_{i-1..i+2}} is the same set of values
+        _, _, cte_m, _, bct_m = orc.recon(S, f[::-1][None, :].copy())
+        assert cte_m[0] == ib and bct_m[0] == pytest.approx(beta, rel=1e-13, abs=0)
+
+
 @pytest.mark.parametrize("K", [6, 8])
 def test_recon_mirror_and_scaling(orc, K):
     """The reconstruction is homogeneous of degree 1 (every stage is scale-covariant) and
