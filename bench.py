@@ -1,9 +1,13 @@
-"""Benchmark: cell-updates per second per SSP-RK3 stage (FP64) of the TENO-M Euler solver.
+"""Benchmark: cell-updates per second per SSP-RK3 stage (FP64) of the TENO-M Euler solver,
+the face kernel's roofline fraction, and the adjoint/forward cost ratio.
 
-Default workload: 2D Euler, 2048 x 2048 periodic, seeded broadband field with four
-circular density/pressure jumps, TENO6-MP, CFL 0.4 (the paper's 2D-shaped workload).
-One step = one SSP-RK3 step (3 stages: CFL reduction, face sweeps on both axes, flux
-difference + stage combine), all on the GPU through the C ABI.
+Default workload: 3D Euler, 256^3 periodic on [0, 2 pi]^3, seeded solenoidal velocity
+(E(k) ~ k^4 exp(-2 (k/4)^2), rms Mach 0.6), TENO8A-M-MP, CFL 0.4 -- the largest of the
+paper-shaped workloads that fits one GPU ("throughput at scale").  One step = one SSP-RK3
+step (3 stages: CFL reduction, face sweeps on the three axes, flux difference + stage
+combine), all on the GPU through the C ABI.  The same line carries the adjoint workload's
+figures (2D 512^2, 200 steps, checkpoints every 20: backward over forward time per step,
+central-difference check on 16 seeded directions at two step sizes).
 
 Prints one JSON line.  --impl reference times the CPU oracle (the deliberately slow,
 plain FP64 restatement of the method) on a bounded sample of the same workload.
@@ -28,6 +32,8 @@ WORKLOADS = {
     "broadband_2d_2048_teno6_mp": ("broadband_2d", (2048, 2048), 6, 0),
     "broadband_2d_2048_teno8_tvd5": ("broadband_2d", (2048, 2048), 8, 1),
     "solenoidal_3d_256_teno8_mp": ("solenoidal_3d", (256, 256, 256), 8, 0),
+    # a smaller case of the same 3D field recipe, for ncu captures (0.5 GB on the device)
+    "solenoidal_3d_128_teno8_mp": ("solenoidal_3d", (128, 128, 128), 8, 0),
 }
 BATCH_WORKLOADS = {
     # name: (problems, seed, nmin, nmax, K, limiter)
@@ -37,8 +43,10 @@ ADJOINT_WORKLOADS = {
     # name: (n, seed, steps, window, checkpoint_every, K, limiter)
     "adjoint_broadband_2d_512_teno6_mp": (512, 5, 200, 64, 20, 6, 0),
 }
-DEFAULT = "broadband_2d_2048_teno6_mp"
+DEFAULT = "solenoidal_3d_256_teno8_mp"
+ADJOINT_DEFAULT = "adjoint_broadband_2d_512_teno6_mp"
 FP64_NOMINAL = 1.25e12  # FLOP/s, GB300 FP64 (an FMA counts 2)
+FP64_LANES_PER_CLK = 304  # FP64 pipe: 2 lanes per clock per SM x 152 SMs
 
 
 FACE_SOURCES = ("tenom_face.cuh", "tenom_recon.cuh", "tenom_linear.cuh", "teno_coeffs.cuh", "tenom_fastmath.cuh",
@@ -81,7 +89,9 @@ def flops_per_face(name):
     key = {"broadband_2d_2048_teno6_mp": ("broadband_2d_2048", "K=6", "lim=MP"),
            "broadband_2d_2048_teno8_tvd5": ("broadband_2d_2048", "K=8", "lim=TVD5"),
            "solenoidal_3d_256_teno8_mp": ("solenoidal_3d_256", "K=8", "lim=MP"),
-           "batched_riemann_512_teno6_mp": ("riemann_1d_batch", "K=6", "lim=MP")}[name]
+           "batched_riemann_512_teno6_mp": ("riemann_1d_batch", "K=6", "lim=MP")}.get(name)
+    if key is None:
+        return None
     with open(os.path.join(ROOT, "tests", "golden", "flops_per_face.txt")) as fh:
         for line in fh:
             parts = line.split()
@@ -287,9 +297,12 @@ def oracle_rate_batch(name, seconds):
 
 def launches_per_step(dim, positivity):
     """Kernel launches of one SSP-RK3 step of a grid workload: the signal-speed reduction, dt
-    and the time update, and per stage the primitives, one face sweep per axis (plus one
-    limiter pass per axis when the positivity limiter is on) and the cell update."""
-    return 3 + 3 * (dim * (2 if positivity else 1) + 2)
+    and the time update, and per stage the primitives and one face sweep per axis, the x
+    sweep carrying the cell update; with the positivity limiter, per stage also one limiter
+    pass per axis and a separate cell-update pass."""
+    if positivity:
+        return 3 + 3 * (2 * dim + 2)
+    return 3 + 3 * (dim + 1)
 
 
 def grid_config(name, ws, positivity):
@@ -427,31 +440,9 @@ def run_ours(args):
     e2e = job_rate(float(ncell) * 3 * e2e_steps, ws, e2e_s)
     state_bytes = 8 * S.nv * ncell
 
-    # roofline of the dominant kernel (face flux): FP64-ALU bound
-    fpf = flops_per_face(name)
-    faces_per_launch = nface / len(shape)
-    achieved = fpf * faces_per_launch / (face_ms * 1e-3) if face_ms > 0 else None
+    # roofline of the dominant kernel (face flux): bound by FP64 instruction issue
     probe = T.fp64_peak()
-    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL, "unit": "FLOP/s",
-            "frac": achieved / FP64_NOMINAL if achieved else None, "traffic": None,
-            "kernel": "face_kernel (fused characteristic TENO-M face flux)",
-            "flops_per_face": fpf, "faces_per_launch": faces_per_launch, "ms_per_launch": face_ms,
-            "launches_timed": face_launches,
-            "peak_note": "nominal GB300 FP64: 2 DFMA lanes/clock/SM x 152 SMs x 2.07 GHz, FMA = 2 flops",
-            "achieved_note": "algorithmic flops = the oracle's per-face count of the textbook method "
-                             "(indicators, comparisons and min/max in FP64); the kernel retires far "
-                             "fewer FP64 operations per face, hence frac > 1",
-            "fp64_probe_flops": probe}
-    fig = profile_figures(name)
-    if fig:
-        fpi = float(fig["fp64_thread_instr_per_face"])
-        mhz = clk.get("sm_mhz") or 2070.0
-        roof["traffic"] = float(fig["dram_bytes_per_launch"])
-        roof["executed"] = {
-            "fp64_thread_instr_per_face": fpi, "fp64_pipe_busy_ncu": float(fig["fp64_pipe_busy"]),
-            "frac_fp64_issue": fpi * faces_per_launch / (face_ms * 1e-3) / (304 * mhz * 1e6) if face_ms > 0 else None,
-            "note": "FP64 instructions the kernel executes (ncu, %s) at the live launch time over the "
-                    "FP64 pipe's 304 lanes per clock" % fig["file"]}
+    roof = face_roofline(name, shape, S.nv, face_ms, face_launches, clk, probe)
     lps = launches_per_step(len(shape), args.positivity)
 
     out = {"metric": "cell-updates/s per RK stage (FP64)", "value": value, "unit": "cell-updates/s",
@@ -463,6 +454,22 @@ def run_ours(args):
                    "d2h_bytes_per_step": state_bytes},
            "gpu_launches": lps * args.steps,
            "roofline": roof, "clocks": clk}
+    # decision statistics of the method at the end state (a logging pass after the timed
+    # region): nonsmooth share per candidate, limiter activity, near-cutoff decisions
+    cnt = None
+    for a in range(len(shape)):
+        cnt = S.decision_stats(U, a, counters=cnt)
+    out["decision_stats"] = decision_summary(T.stats_dict(cnt.cpu().numpy(), K), K)
+    if args.decision_log:
+        with open(args.decision_log, "a") as fh:
+            fh.write(json.dumps({"workload": name, "steps": args.warmup + args.steps + e2e_steps + 1,
+                                 "state": "end of the run", **out["decision_stats"]}) + "\n")
+    S.close()
+    del U, U0, host_in, host_out
+    torch.cuda.empty_cache()
+    if ws == 1 and name == DEFAULT and not args.no_adjoint:
+        # the metric's second figure: the adjoint workload's cost ratio, in the same process
+        out["adjoint"] = measure_adjoint(ADJOINT_DEFAULT, fd_dirs=args.fd_dirs)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         r, sample, el = oracle_rate(name, seconds=args.ref_seconds or 12.0, seed=args.seed)
         ra, cores, sample_all = oracle_rate_all_cores(name, oracle_rate.rows, seed=args.seed)
@@ -471,9 +478,82 @@ def run_ours(args):
                                "single_thread": {"value": r, "cores": 1, "sample": sample}}
     if rank == 0:
         print(json.dumps(out), flush=True)
-    S.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def decision_summary(c, K):
+    """Shares of the counters of tenom_decision_stats (per split side: face x characteristic
+    field x f+/f-)."""
+    n = max(c["sides"], 1)
+    out = {"sides": c["sides"], "counts": c,
+           "nonsmooth_share_per_k": [c["nonsmooth_k%d" % k] / n for k in range(K - 2)],
+           "all_smooth_share": c["all_smooth"] / n, "limited_share": c["limited_sides"] / n,
+           "limiter_changed_per_side": c["limiter_changed"] / n,
+           "certified_share": c["certified"] / n, "certified_disagree": c["certified_disagree"],
+           "near_cutoff_decisions": c["near_cutoff"], "near_cutoff_sides": c["near_cutoff_sides"],
+           "near_integer_beta": c["near_integer_beta"]}
+    ct = [c["ct_exp_%d" % e] for e in (7, 8, 9, 10)]
+    if sum(ct):
+        out["adaptive_ct_share"] = {"1e-%d" % e: v / n for e, v in zip((7, 8, 9, 10), ct)}
+    return out
+
+
+def face_roofline(name, shape, nv, face_ms, face_launches, clk, probe_flops):
+    """Roofline of the face kernel.  The kernel is bound by FP64 instruction issue (about 36
+    algorithmic flops per byte against a ridge point of 0.2), so the bound is the FP64
+    pipe: achieved = FP64 thread instructions per face (ncu count of DFMA + DADD + DMUL,
+    committed under profiles/ for these kernel sources) x faces per launch / the CUDA-event
+    launch time of the timed region; peak = the DFMA probe's measured instruction rate
+    (the pool's peaks file has no FP64 figure).  HBM use and the oracle's op count per
+    face (the textbook formulation's work rate) are reported beside it, not as the
+    fraction."""
+    ncell = 1
+    for m in shape:
+        ncell *= m
+    faces_per_launch = sum(ncell // shape[a] * (shape[a] + 1) for a in range(len(shape))) / len(shape)
+    probe_inst = probe_flops / 2.0  # the probe counts an FMA as 2 flops
+    smax = clk.get("sm_max_mhz") or 2070.0
+    fig = profile_figures(name)
+    ipf = float(fig["fp64_thread_instr_per_face"]) if fig else None
+    achieved = ipf * faces_per_launch / (face_ms * 1e-3) if ipf and face_ms > 0 else None
+    alg_bytes = (nv + (nv + 2) + nv) * 8 * faces_per_launch  # read U and the primitives, write the fluxes
+    hbm_peak = measured_hbm_gbs()
+    roof = {"bound": "alu", "achieved": achieved, "peak": probe_inst, "unit": "FP64 inst/s",
+            "frac": achieved / probe_inst if achieved else None,
+            "traffic": float(fig["dram_bytes_per_launch"]) if fig else None,
+            "kernel": "face_kernel (fused characteristic TENO-M face flux)",
+            "fp64_inst_per_face": ipf, "faces_per_launch": faces_per_launch, "ms_per_launch": face_ms,
+            "launches_timed": face_launches,
+            "peak_note": "measured: DFMA probe (8 independent FMA chains per thread) in FP64 instructions/s; "
+                         "nominal %d lanes/clock x %.0f MHz = %.3g inst/s" % (FP64_LANES_PER_CLK, smax,
+                                                                              FP64_LANES_PER_CLK * smax * 1e6),
+            "achieved_note": ("ncu FP64 thread instructions per face from %s (same kernel sources) x faces per "
+                              "launch / CUDA-event launch time" % fig["file"]) if fig else
+                             "no ncu count for these kernel sources: achieved and traffic unmeasured",
+            "hbm": {"algorithmic_bytes_per_launch": alg_bytes,
+                    "achieved_gbs": alg_bytes / (face_ms * 1e-3) / 1e9 if face_ms > 0 else None,
+                    "peak_gbs": hbm_peak, "frac": (alg_bytes / (face_ms * 1e-3) / 1e9 / hbm_peak)
+                    if face_ms > 0 and hbm_peak else None}}
+    if fig:
+        roof["fp64_pipe_busy_ncu"] = float(fig["fp64_pipe_busy"])
+    fpf = flops_per_face(name)
+    if fpf and face_ms > 0:
+        roof["oracle_equivalent_rate"] = {
+            "flops_per_face": fpf, "flop_per_s": fpf * faces_per_launch / (face_ms * 1e-3),
+            "note": "the oracle's op count of the textbook formulation (indicators, comparisons and "
+                    "min/max in FP64, no central shortcut) per face over the launch time; the kernel "
+                    "retires far fewer FP64 operations, so this rate is not bounded by the FP64 peak"}
+    return roof
+
+
+def measured_hbm_gbs():
+    """HBM copy bandwidth of this machine's GPUs (GB/s) from the generated peaks file."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return None
 
 
 def run_batch(args):
@@ -857,26 +937,22 @@ def run_le_blanc(args):
     print(json.dumps(out), flush=True)
 
 
-def run_adjoint(args):
+def measure_adjoint(name, tape="auto", rollout_steps=0, fd_dirs=16, fd_steps=(1e-8, 1e-7)):
     """Adjoint workload: 2D 512^2 broadband field with circular jumps, TENO6-MP, 200 SSP-RK3
     steps at a fixed dt, loss = integral of p over a seeded 64 x 64 window at the end;
     gradient with respect to the initial density through the frozen-branch adjoint with
-    checkpoints every 20 steps (torch.autograd); central differences on 16 seeded unit
-    directions.  Reports the backward pass's cell-updates/s per RK stage and the
-    adjoint/forward cost ratio per step."""
+    checkpoints every 20 steps (torch.autograd); central differences on fd_dirs seeded
+    unit directions at each step size in fd_steps.  Returns the figures as a dict: forward
+    and backward device time per step (CUDA events on the stream), their ratio, the
+    backward pass's cell-updates/s per RK stage, and the central-difference errors."""
     import numpy as np
     import torch
-    torch.cuda.set_device(0)
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_2010_13289_gb300 import problems as PB
     from paper_2010_13289_gb300 import tenom as T
     from paper_2010_13289_gb300.autograd import rollout
-    name = args.workload
     n, seed, steps, win_n, every, K, lim = ADJOINT_WORKLOADS[name]
-    if args.rollout_steps:  # shorter rollouts for profiling runs (not the workload's number)
-        steps = args.rollout_steps
-    ndirs = args.fd_dirs
+    if rollout_steps:  # shorter rollouts for profiling runs (not the workload's number)
+        steps = rollout_steps
     prim, dx = PB.broadband_2d(n, seed)
     rng = np.random.default_rng(seed)
     wy, wx = rng.integers(0, n - win_n, 2)
@@ -886,7 +962,7 @@ def run_adjoint(args):
     dt = S.max_dt(S.init_state(primd), 0.4).item()
     gam = 1.4
     stream = torch.cuda.current_stream()
-    tape = "linear" if _linear_tape(S, min(every, steps), args.tape) else "flags"
+    tape = "linear" if _linear_tape(S, min(every, steps), tape) else "flags"
 
     def loss_of(rho0, grad=False):
         pr = primd.clone()
@@ -903,7 +979,7 @@ def run_adjoint(args):
     L, U0 = loss_of(primd[0], grad=True)
     L.backward()
     torch.cuda.synchronize()
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
     e0.record(stream)
@@ -919,39 +995,64 @@ def run_adjoint(args):
     u, v = primd[1], primd[2]
     grad_rho = Ub[0] + u * Ub[1] + v * Ub[2] + 0.5 * (u * u + v * v) * Ub[3]
     gnorm = float(torch.linalg.norm(grad_rho))
-    # central differences on 16 seeded unit directions (step 1e-8)
+    # central differences on seeded unit directions, at each step size
     rng = np.random.default_rng(seed + 16)
-    fd_err = []
+    dirs = [rng.normal(size=(n, n)) for _ in range(fd_dirs)]
+    fd = {}
     with torch.no_grad():
-        for _ in range(ndirs):
-            d = torch.from_numpy(rng.normal(size=(n, n))).cuda()
-            d /= torch.linalg.norm(d)
-            Lp, _ = loss_of(primd[0] + 1e-8 * d)
-            Lm, _ = loss_of(primd[0] - 1e-8 * d)
-            fd = (Lp - Lm).item() / 2e-8
-            ad = float((grad_rho * d).sum())
-            fd_err.append(abs(fd - ad) / gnorm)
-    ncell = n * n
-    value = float(ncell) * 3 * steps / (bwd_ms * 1e-3)
-    out = {"metric": "cell-updates/s per RK stage (FP64)", "value": value, "unit": "cell-updates/s",
-           "n_gpus": 1, "steps": steps, "warmup": 1, "ms_per_step": bwd_ms / steps, "higher_is_better": True,
+        for h in fd_steps:
+            errs, rel = [], []
+            for dv in dirs:
+                d = torch.from_numpy(dv).cuda()
+                d /= torch.linalg.norm(d)
+                Lp, _ = loss_of(primd[0] + h * d)
+                Lm, _ = loss_of(primd[0] - h * d)
+                fdv = (Lp - Lm).item() / (2 * h)
+                ad = float((grad_rho * d).sum())
+                errs.append(abs(fdv - ad) / gnorm)
+                rel.append(abs(fdv - ad) / max(abs(ad), 1e-300))
+            fd["%g" % h] = {"max_err_over_grad_norm": max(errs) if errs else None,
+                            "median_err_over_grad_norm": float(np.median(errs)) if errs else None,
+                            "median_err_over_directional_derivative": float(np.median(rel)) if rel else None}
+    best = min(fd, key=lambda k: fd[k]["max_err_over_grad_norm"]) if fd else None
+    S.close()
+    return {"workload": name, "shape": [n, n], "K": K, "limiter": "MP" if lim == 0 else "TVD5", "steps": steps,
+            "window": win_n, "checkpoint_every": every, "dt": dt, "tape": tape,
+            "adjoint_forward_ratio": bwd_ms / fwd_ms,
+            "forward_ms_per_step": fwd_ms / steps, "backward_ms_per_step": bwd_ms / steps,
+            "backward_cell_updates_per_s": float(n * n) * 3 * steps / (bwd_ms * 1e-3),
+            "loss": L.item(), "grad_norm": gnorm,
+            "fd_check": {"directions": fd_dirs, "by_step": fd, "best_step": best,
+                         "max_err_over_grad_norm": fd[best]["max_err_over_grad_norm"] if best else None,
+                         "note": "central differences of the full forward (cutoff, limiter and LLF switches "
+                                 "included) against the frozen-branch adjoint; error / |gradient|"},
+            "clocks": clk}
+
+
+def run_adjoint(args):
+    """The adjoint workload on its own line: the backward pass's cell-updates/s per RK stage
+    as the value, with the adjoint/forward cost ratio and the central-difference check."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    r = measure_adjoint(args.workload, tape=args.tape, rollout_steps=args.rollout_steps, fd_dirs=args.fd_dirs)
+    n = r["shape"][0]
+    out = {"metric": "cell-updates/s per RK stage (FP64)", "value": r["backward_cell_updates_per_s"],
+           "unit": "cell-updates/s", "n_gpus": 1, "steps": r["steps"], "warmup": 1,
+           "ms_per_step": r["backward_ms_per_step"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded, shaped like the paper's workloads)",
-           "config": {"workload": name, "shape": [n, n], "K": K, "limiter": "MP" if lim == 0 else "TVD5",
-                      "window": win_n, "checkpoint_every": every, "dt": dt,
+           "config": {"workload": args.workload, "shape": [n, n], "K": r["K"], "limiter": r["limiter"],
+                      "window": r["window"], "checkpoint_every": r["checkpoint_every"], "dt": r["dt"],
                       "l2": "the forward state (8 MB) fits in L2; the backward streams the recorded "
                             "linearisation (GBs per segment) from HBM",
-                      "tape": tape,
+                      "tape": r["tape"],
                       "pass": "backward (frozen-branch adjoint, segment recomputation included)"},
-           "adjoint_forward_ratio": bwd_ms / fwd_ms,
-           "forward_ms_per_step": fwd_ms / steps, "backward_ms_per_step": bwd_ms / steps,
-           "loss": L.item(), "grad_norm": gnorm,
-           "fd_check": {"directions": ndirs, "step": 1e-8,
-                        "max_err_over_grad_norm": max(fd_err) if fd_err else None,
-                        "median_err_over_grad_norm": float(np.median(fd_err)) if fd_err else None},
-           "clocks": clk}
+           "adjoint_forward_ratio": r["adjoint_forward_ratio"],
+           "forward_ms_per_step": r["forward_ms_per_step"], "backward_ms_per_step": r["backward_ms_per_step"],
+           "loss": r["loss"], "grad_norm": r["grad_norm"], "fd_check": r["fd_check"], "clocks": r["clocks"]}
     print(json.dumps(out), flush=True)
-    S.close()
 
 
 def main():
@@ -973,6 +1074,10 @@ def main():
                     help="adjoint workloads: rollout length (default: the workload's 200); for profiling runs")
     ap.add_argument("--fd-dirs", type=int, default=16,
                     help="adjoint workloads: finite-difference directions (default 16)")
+    ap.add_argument("--decision-log", default=None,
+                    help="grid workloads: append the decision statistics as a JSON line to this file")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="default workload: leave out the adjoint workload's figures")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -159,6 +159,22 @@ tenom_status tenom_positivity_limit(tenom_ctx* ctx, const double* U, int axis, c
  * [beta] - 7 of Eq. cut-off_adjust when C_T is adaptive.  flags may be NULL. */
 tenom_status tenom_face_dump(tenom_ctx* ctx, const double* U, int axis, double* Fhat, uint8_t* flags);
 
+/* Decision statistics of the reconstruction at the state U (device [nvar][ncell]) on the
+ * faces of axis `axis`, for logging (not part of a step): the face kernel's characteristic
+ * sequences (f+ and f- of every field, Section 4) are examined instead of reconstructed,
+ * and TENOM_NSTATS counters are ADDED to the caller-owned device array counters_dev (64-bit;
+ * the caller zeroes it).  Per split side: [0] sides; [1] sides the certified FP32 cutoff
+ * filter decided, [2] of which its decisions differ from the FP64 ones (rounding-decided);
+ * [3] sides with every candidate smooth; [4 + k], k = 0..K-3: candidates k judged nonsmooth
+ * (delta_k = 0, Eq. cut-off); [10] sides where the limiter runs (any nonsmooth candidate,
+ * Eq. mp_flux); [11] nonsmooth candidates whose value the limiter changed; [12] decisions
+ * within 1e-10 relative of the cutoff (|chi_k - C_T| <= 1e-10 C_T), [13] sides with one;
+ * [14 + j]: adaptive exponent [beta] = 7 + j of TENO8A (Eq. cut-off_adjust), [18] sides
+ * with beta within 1e-10 of an integer; [19] sides with a non-finite sum of gamma.
+ * Stream-ordered.  Returns TENOM_E_INVALID for a bad axis or pointer. */
+#define TENOM_NSTATS 20
+tenom_status tenom_decision_stats(tenom_ctx* ctx, const double* U, int axis, unsigned long long* counters_dev);
+
 /* ---------------------------------------------------------------- batched 1D problems
  * Many independent 1D Euler problems of uneven size advanced together (each problem as in
  * tenom_advance, on its own grid, time and CFL step).  State: one caller-owned device array
@@ -202,9 +218,13 @@ tenom_status tenom_batch_set_tiling(tenom_batch* b, int tile, int ctas_per_sm);
  * counterpart: this entry point exists for callers that must not allocate device memory
  * once they are running -- code living inside another framework's memory pool or
  * allocator hook, or a latency-critical loop that cannot accept the implicit device
- * synchronisation of cudaMalloc/cudaFree.  It computes dUdt = L(U) exactly like tenom_rhs
- * (same kernels) for the given grid and scheme, on `stream` (a cudaStream_t; NULL = legacy
- * default stream).  U and dUdt are caller-owned device arrays as for tenom_rhs; status_dev
+ * synchronisation of cudaMalloc/cudaFree.  It computes dUdt = L(U) for the given grid and
+ * scheme, on `stream` (a cudaStream_t; NULL = legacy default stream), with the face-sweep
+ * and flux-difference kernels of tenom_rhs.  One difference: tenom_rhs first computes the
+ * cells' primitives (velocity, p, H, c, sqrt rho) once per cell into its context's
+ * buffer, while this call has no such buffer and the face kernels form them for each
+ * staged point of their tile; the two orders of evaluation round alike except in the last
+ * bits (agreement to 1e-13 relative is tested).  U and dUdt are caller-owned device arrays as for tenom_rhs; status_dev
  * is an optional caller-owned device int that receives TENOM_ST_* bits (ORed in, the
  * caller clears it); with NULL the bits go to a word inside the scratch and are not
  * reported.

@@ -36,29 +36,20 @@ __global__ void init_state_kernel(const double* __restrict__ prim, double* __res
 }
 
 struct StageArgs {
-  const double* F[3];  /* face buffers per axis [NV][nface_a] */
-  const double* U0;    /* U^n (stages 2, 3) */
-  const double* Us;    /* stage input state */
-  double* out;         /* stage output or dU/dt */
-  const double* dt;    /* device dt (null for rhs) */
-  const double* t;     /* device time: steps at t >= t_end are skipped */
+  CellUpdate cu;       /* faces of every axis, states, dt, 1/dx_a, stage coefficients */
   int n[3];
-  double rdx[3];       /* 1 / dx_a */
   long long ncell;
-  long long nface[3];
-  double cA, cB;       /* out = cA U0 + cB (Us + dt L); cA = 0, cB = 1 for stage 1 */
-  int mode;            /* 0: rhs, 1: stage 1, 2: stages 2/3 */
-  double t_end;
 };
 
 /* Flux difference -sum_a (F_{a,i+1/2} - F_{a,i-1/2})/dx_a (Eq. approximateEq) fused with
-   the SSP-RK3 stage combine; 1/dx_a is formed once on the host (an FP64 division per cell
-   and axis would occupy the FP64 pipe longer than the kernel's memory traffic takes). */
+   the SSP-RK3 stage combine (cell_update, shared with the fused x sweep so that both give
+   the same bits); 1/dx_a is formed once on the host (an FP64 division per cell and axis
+   would occupy the FP64 pipe longer than the kernel's memory traffic takes). */
 template <int NV>
 __global__ void stage_kernel(const StageArgs A) {
   constexpr int DIM = NV - 2;
   const long long nc = A.ncell;
-  const double dt = (A.mode != 0) ? *A.dt : 0.0;
+  const double dt = (A.cu.mode != 0) ? *A.cu.dt : 0.0;
   /* one thread per cell: x from the block's column, y and z from the grid (strided when an
      axis exceeds the grid's 65535 limit) */
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -67,9 +58,8 @@ __global__ void stage_kernel(const StageArgs A) {
     for (int y = blockIdx.y; y < A.n[1]; y += gridDim.y) {
       const long long yz = y + (long long)A.n[1] * z;
       const long long c = x + (long long)A.n[0] * yz;
-      long long fl[3], fs[3];
-      fl[0] = x + (long long)(A.n[0] + 1) * yz;
-      fs[0] = 1;
+      long long fl[3] = {0, 0, 0}, fs[3] = {0, 0, 0};
+      const long long fx = x + (long long)(A.n[0] + 1) * yz;
       if (DIM > 1) {
         fl[1] = x + (long long)A.n[0] * (y + (long long)(A.n[1] + 1) * z);
         fs[1] = A.n[0];
@@ -78,25 +68,13 @@ __global__ void stage_kernel(const StageArgs A) {
         fl[2] = c;
         fs[2] = (long long)A.n[0] * A.n[1];
       }
+      double dfx[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        double r = 0.0;
-#pragma unroll
-        for (int a = 0; a < DIM; ++a) {
-          const double* F = A.F[a] + v * A.nface[a];
-          r = r - (F[fl[a] + fs[a]] - F[fl[a]]) * A.rdx[a];
-        }
-        if (A.mode == 0) {
-          A.out[v * nc + c] = r;
-        } else if (dt == 0.0) {
-          /* a step past t_end: every stage state equals U^n, keep it bit for bit */
-          A.out[v * nc + c] = A.Us[v * nc + c];
-        } else {
-          const double us = A.Us[v * nc + c];
-          const double t1 = us + dt * r;
-          A.out[v * nc + c] = (A.mode == 1) ? t1 : A.cA * A.U0[v * nc + c] + A.cB * t1;
-        }
+        const double* F = A.cu.F[0] + v * A.cu.nface[0];
+        dfx[v] = F[fx + 1] - F[fx];
       }
+      cell_update<NV>(A.cu, nc, c, dfx, fl, fs, dt);
     }
   }
 }
@@ -347,7 +325,8 @@ struct tenom_ctx {
   int nv;
   long long ncell;
   long long nface[3];
-  double* W1;          /* stage buffer */
+  double* W1;          /* stage buffers: stage 1 writes W1, stage 2 reads W1 and writes W2 */
+  double* W2;
   double* face[3];     /* face buffers */
   double* P;           /* per-cell primitives of the stage being evaluated ([nvar + 2][ncell]) */
   double* dt;          /* device dt */
@@ -482,7 +461,9 @@ tenom_status tenom_create(tenom_ctx** out, const tenom_grid* grid, const tenom_s
   c->ev_used = 0;
   c->face_ms = 0;
   c->face_launches = 0;
+  c->W2 = nullptr;
   cudaError_t e = cudaMalloc(&c->W1, sizeof(double) * c->nv * c->ncell);
+  if (e == cudaSuccess) e = cudaMalloc(&c->W2, sizeof(double) * c->nv * c->ncell);
   for (int a = 0; a < grid->dim && e == cudaSuccess; ++a) e = cudaMalloc(&c->face[a], sizeof(double) * c->nv * c->nface[a]);
   if (e == cudaSuccess) e = cudaMalloc(&c->P, sizeof(double) * (c->nv + 2) * c->ncell);
   if (e == cudaSuccess) e = cudaMalloc(&c->dt, sizeof(double) * 2);
@@ -506,6 +487,7 @@ tenom_status tenom_destroy(tenom_ctx* c) {
   if (!c) return TENOM_OK;
   cudaStreamSynchronize(c->st);
   cudaFree(c->W1);
+  cudaFree(c->W2);
   for (int a = 0; a < 3; ++a) cudaFree(c->face[a]);
   cudaFree(c->P);
   cudaFree(c->dt);
@@ -557,11 +539,15 @@ static FaceArgs face_args(tenom_ctx* c, const double* U, int axis, double* F, ui
   return a;
 }
 
+/* one face sweep of axis `axis` at U (P: its cell primitives); with cu (axis 0 only) the x
+   sweep also applies the cell update (flux difference, stage combine) instead of writing
+   its faces */
 static cudaError_t launch_faces(tenom_ctx* c, const double* U, int axis, double* F, uint8_t* flags,
-                                double* lin = nullptr, const double* P = nullptr) {
+                                double* lin = nullptr, const double* P = nullptr, const CellUpdate* cu = nullptr) {
   FaceArgs a = face_args(c, U, axis, F, flags);
   a.lin = lin;
   a.P = P;
+  if (cu) a.cu = *cu;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->timing) {
     while (c->ev.size() < c->ev_used + 2) {
@@ -576,7 +562,11 @@ static cudaError_t launch_faces(tenom_ctx* c, const double* U, int axis, double*
     cudaEventRecord(e0, c->st);
   }
   cudaError_t e;
-  if (lin) {
+  if (cu) {
+    if (c->nv == 3) e = launch_fused_nv3(a, c->s.K, c->s.limiter, c->st);
+    else if (c->nv == 4) e = launch_fused_nv4(a, c->s.K, c->s.limiter, c->st);
+    else e = launch_fused_nv5(a, c->s.K, c->s.limiter, c->st);
+  } else if (lin) {
     if (c->nv == 3) e = launch_face_rec_nv3(a, axis, c->s.K, c->s.limiter, c->st);
     else if (c->nv == 4) e = launch_face_rec_nv4(a, axis, c->s.K, c->s.limiter, c->st);
     else e = launch_face_rec_nv5(a, axis, c->s.K, c->s.limiter, c->st);
@@ -589,24 +579,32 @@ static cudaError_t launch_faces(tenom_ctx* c, const double* U, int axis, double*
   return e;
 }
 
+static CellUpdate cell_update_args(tenom_ctx* c, const double* U0, const double* Us, double* out, int mode, double cA,
+                                   double cB) {
+  CellUpdate u;
+  memset(&u, 0, sizeof(u));
+  for (int d = 0; d < 3; ++d) {
+    u.F[d] = c->face[d];
+    u.rdx[d] = 1.0 / c->g.dx[d];
+    u.nface[d] = c->nface[d];
+  }
+  u.U0 = U0;
+  u.Us = Us;
+  u.out = out;
+  u.dt = c->dt;
+  u.cA = cA;
+  u.cB = cB;
+  u.mode = mode;
+  return u;
+}
+
 static cudaError_t launch_stage(tenom_ctx* c, const double* U0, const double* Us, double* out, int mode, double cA,
                                 double cB) {
   StageArgs a;
   memset(&a, 0, sizeof(a));
-  for (int d = 0; d < 3; ++d) {
-    a.F[d] = c->face[d];
-    a.n[d] = c->g.n[d];
-    a.rdx[d] = 1.0 / c->g.dx[d];
-    a.nface[d] = c->nface[d];
-  }
-  a.U0 = U0;
-  a.Us = Us;
-  a.out = out;
-  a.dt = c->dt;
+  a.cu = cell_update_args(c, U0, Us, out, mode, cA, cB);
+  for (int d = 0; d < 3; ++d) a.n[d] = c->g.n[d];
   a.ncell = c->ncell;
-  a.cA = cA;
-  a.cB = cB;
-  a.mode = mode;
   return launch_stage_kernel(c->nv, a, c->st);
 }
 
@@ -626,11 +624,23 @@ static cudaError_t eval_faces(tenom_ctx* c, const double* U) {
   return e;
 }
 
+/* One evaluation of the operator at Us with the cell update fused into the x sweep: the
+   primitives, the sweeps of the other axes (faces to their buffers), then the x sweep,
+   which differences its faces in the tile and writes out = the stage combine of mode
+   (out must not be Us: other tiles still read Us). */
+static cudaError_t fused_stage(tenom_ctx* c, const double* Us, const double* U0, double* out, int mode, double cA,
+                               double cB) {
+  cudaError_t e = launch_prims(c, Us);
+  for (int a = 1; a < c->g.dim && e == cudaSuccess; ++a) e = launch_faces(c, Us, a, c->face[a], nullptr, nullptr, c->P);
+  if (e != cudaSuccess) return e;
+  const CellUpdate cu = cell_update_args(c, U0, Us, out, mode, cA, cB);
+  return launch_faces(c, Us, 0, nullptr, nullptr, nullptr, c->P, &cu);
+}
+
 tenom_status tenom_rhs(tenom_ctx* c, const double* U, double* dUdt) {
   if (!c) return TENOM_E_INVALID;
   if (!aligned8(U) || !aligned8(dUdt) || U == dUdt) return fail(c, TENOM_E_INVALID, "rhs: bad pointers");
-  cudaError_t e = eval_faces(c, U);
-  if (e == cudaSuccess) e = launch_stage(c, nullptr, U, dUdt, 0, 0.0, 0.0);
+  cudaError_t e = fused_stage(c, U, nullptr, dUdt, 0, 0.0, 0.0);
   return e == cudaSuccess ? TENOM_OK : cuda_fail(c, e, "rhs");
 }
 
@@ -688,8 +698,17 @@ static cudaError_t stage_faces(tenom_ctx* c, const double* Us) {
   return e;
 }
 
-/* three stages; dt already in c->dt */
+/* three stages; dt already in c->dt.  Without the positivity limiter each stage is one
+   fused evaluation (stage 2 writes W2, so that no stage overwrites the state its x sweep
+   reads); the limiter needs every face of the stage before any cell update, so with it the
+   faces go through their buffers and a separate cell-update pass. */
 static cudaError_t rk3_core(tenom_ctx* c, double* U) {
+  if (c->s.positivity != TENOM_PP_ON) {
+    cudaError_t e = fused_stage(c, U, nullptr, c->W1, 1, 0.0, 1.0);
+    if (e == cudaSuccess) e = fused_stage(c, c->W1, U, c->W2, 2, 0.75, 0.25);
+    if (e == cudaSuccess) e = fused_stage(c, c->W2, U, U, 2, 1.0 / 3.0, 2.0 / 3.0);
+    return e;
+  }
   cudaError_t e = stage_faces(c, U);
   if (e == cudaSuccess) e = launch_stage(c, nullptr, U, c->W1, 1, 0.0, 1.0);
   if (e == cudaSuccess) e = stage_faces(c, c->W1);
@@ -766,6 +785,23 @@ tenom_status tenom_face_dump(tenom_ctx* c, const double* U, int axis, double* Fh
   cudaError_t e = launch_faces(c, U, axis, Fhat, flags);
   c->timing = t;
   return e == cudaSuccess ? TENOM_OK : cuda_fail(c, e, "face_dump");
+}
+
+tenom_status tenom_decision_stats(tenom_ctx* c, const double* U, int axis, unsigned long long* counters_dev) {
+  static_assert(TENOM_NSTATS == SC_COUNT, "counter layout of the header and the kernels");
+  if (!c) return TENOM_E_INVALID;
+  if (axis < 0 || axis >= c->g.dim) return fail(c, TENOM_E_INVALID, "decision_stats: bad axis");
+  if (!aligned8(U) || !aligned8(counters_dev)) return fail(c, TENOM_E_INVALID, "decision_stats: bad pointers");
+  cudaError_t e = launch_prims(c, U);
+  if (e == cudaSuccess) {
+    FaceArgs a = face_args(c, U, axis, nullptr, nullptr);
+    a.P = c->P;
+    a.stats = counters_dev;
+    if (c->nv == 3) e = launch_stats_nv3(a, axis, c->s.K, c->s.limiter, c->st);
+    else if (c->nv == 4) e = launch_stats_nv4(a, axis, c->s.K, c->s.limiter, c->st);
+    else e = launch_stats_nv5(a, axis, c->s.K, c->s.limiter, c->st);
+  }
+  return e == cudaSuccess ? TENOM_OK : cuda_fail(c, e, "decision_stats");
 }
 
 tenom_status tenom_status_word(tenom_ctx* c, int* status_host, int reset) {
@@ -1082,14 +1118,14 @@ cudaError_t launch_rhs_divergence(int nv, double* const F[3], const int n[3], co
   StageArgs a;
   memset(&a, 0, sizeof(a));
   for (int d = 0; d < 3; ++d) {
-    a.F[d] = F[d];
+    a.cu.F[d] = F[d];
     a.n[d] = n[d];
-    a.rdx[d] = 1.0 / dx[d];
-    a.nface[d] = nface[d];
+    a.cu.rdx[d] = 1.0 / dx[d];
+    a.cu.nface[d] = nface[d];
   }
-  a.out = out;
+  a.cu.out = out;
   a.ncell = ncell;
-  a.mode = 0;
+  a.cu.mode = 0;
   return launch_stage_kernel(nv, a, st);
 }
 

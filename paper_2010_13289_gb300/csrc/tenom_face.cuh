@@ -16,9 +16,53 @@
 #include <cstdint>
 #include "tenom_recon.cuh"
 #include "tenom_linear.cuh"
+#include "tenom_stats.cuh"
 #include "tenom_fastmath.cuh"
 
 namespace tenom {
+
+/* Flux difference -sum_a (F_{a,i+1/2} - F_{a,i-1/2}) / dx_a (Eq. approximateEq) and the
+   SSP-RK3 stage combine of one cell: mode 0 out = L (operator), 1 out = Us + dt L (stage
+   1), 2 out = cA U0 + cB (Us + dt L) (stages 2, 3); dt = 0 (a step past t_end) keeps Us. */
+struct CellUpdate {
+  const double* F[3];  /* face buffers per axis [NV][nface_a] (the fused x sweep reads F[1], F[2]) */
+  const double* U0;    /* U^n (stages 2, 3) */
+  const double* Us;    /* stage input state */
+  double* out;         /* stage output or dU/dt (never Us when fused into the x sweep) */
+  const double* dt;    /* device dt (null for the operator) */
+  double rdx[3];       /* 1 / dx_a */
+  long long nface[3];
+  double cA, cB;
+  int mode;
+};
+
+/* the cell update of cell c whose x-face difference F_{x,i+1/2} - F_{x,i-1/2} is dfx; the
+   other axes' faces at fl[a] and fl[a] + fs[a] */
+template <int NV>
+__device__ __forceinline__ void cell_update(const CellUpdate& A, long long nc, long long c, const double (&dfx)[NV],
+                                            const long long (&fl)[3], const long long (&fs)[3], double dt) {
+  constexpr int DIM = NV - 2;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double r = 0.0;
+    r = r - dfx[v] * A.rdx[0];
+#pragma unroll
+    for (int a = 1; a < DIM; ++a) {
+      const double* F = A.F[a] + v * A.nface[a];
+      r = r - (F[fl[a] + fs[a]] - F[fl[a]]) * A.rdx[a];
+    }
+    if (A.mode == 0) {
+      A.out[v * nc + c] = r;
+    } else if (dt == 0.0) {
+      /* a step past t_end: every stage state equals U^n, keep it bit for bit */
+      A.out[v * nc + c] = A.Us[v * nc + c];
+    } else {
+      const double us = A.Us[v * nc + c];
+      const double t1 = us + dt * r;
+      A.out[v * nc + c] = (A.mode == 1) ? t1 : A.cA * A.U0[v * nc + c] + A.cB * t1;
+    }
+  }
+}
 
 struct FaceArgs {
   const double* U;    /* [NV][ncell] */
@@ -27,12 +71,14 @@ struct FaceArgs {
   const double* P;    /* point primitives [NV + 2][ncell] (velocity, p, H, c, sqrt rho), or null */
   double* lin;        /* linearisation [NV][2K+2][nface] (record kernels only) */
   int* status;        /* sticky status word */
+  unsigned long long* stats;  /* decision statistics [SC_COUNT] (statistics kernels only) */
   int n[3];
   int bc[3];
   long long ncell;
   long long nface;
   double gamma;
   SchemeDev sch;
+  CellUpdate cu;      /* the fused x sweep's cell update (FUSE kernels only) */
 };
 
 /* shared-memory layout of the staged point quantities: component c of point p at c * NP + p */
@@ -49,6 +95,11 @@ constexpr int FX_FACES = 128;  /* faces per CTA, x sweeps */
    come from the per-stage kernel) */
 __host__ __device__ constexpr int ft_faces(int K) { return (void)K, 4; }
 constexpr int QSLOTS = 64;     /* reconstruction queue items per warp: two sides x 32 lanes */
+/* resident CTAs per SM the face kernels are compiled for: 3 x 128 threads leave 168
+   registers a thread (K = 8 with the deferred queue spills about 130 bytes a thread to
+   local memory at this budget and still runs 8 % faster on the 3D workload than with 214
+   registers at 2 CTAs per SM) */
+constexpr int FACE_CTAS_PER_SM = 3;
 
 template <int NV, int K, int AXIS>
 struct FaceTile {
@@ -251,11 +302,11 @@ __device__ __forceinline__ void recon_pair_queued(const double (&vp)[K], const d
    sigma_q = (op_q + om_{K-1-q})/2, delta_q = op_q - om_{K-1-q}.
    wq (may be null): this warp's reconstruction queue (recon_pair_queued), shared by the
    lanes in am, which must all make this call; null: each lane reconstructs its own sides. */
-template <int NV, int K, int LIM, int AXIS, int LANES, bool REC = false>
+template <int NV, int K, int LIM, int AXIS, int LANES, bool REC = false, bool STATS = false>
 __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf, int lane, double gamma,
                                                const SchemeDev& sch, double (&Fh)[NV], uint8_t* flags, int& st,
                                                double* lin = nullptr, long long lstride = 0, double* wq = nullptr,
-                                               unsigned am = 0u) {
+                                               unsigned am = 0u, unsigned* cnt = nullptr) {
   using L = PointLayout<NV>;
   constexpr int D = NV - 2;
   constexpr int H = K / 2;
@@ -317,7 +368,7 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
      reconstruction are collected over all fields (flushed early only when full) and worked
      through together; their back-projection and flags follow the flush.  Per (field, side)
      entry e = 2s + side: qmask bit e, queue index in 6-bit field e of qslot. */
-  constexpr bool DQ = !REC && K == 6;  /* K = 8: per-field queue (register budget) */
+  constexpr bool DQ = !REC && !STATS;
   unsigned qmask = 0u;
   unsigned long long qslot = 0ull;
   int nq = 0;
@@ -446,6 +497,11 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
     double vm[K];
 #pragma unroll
     for (int q = 0; q < K; ++q) vm[q] = gm[K - 1 - q];
+    if constexpr (STATS) {  /* statistics of both sides' decisions instead of the flux */
+      side_stats<K, LIM>(gp, sch, *reinterpret_cast<unsigned(*)[SC_COUNT]>(cnt));
+      side_stats<K, LIM>(vm, sch, *reinterpret_cast<unsigned(*)[SC_COUNT]>(cnt));
+      continue;
+    }
     unsigned flp, flm;
     double op[REC ? K : 1], om[REC ? K : 1];
     double fplus, fminus;
@@ -519,9 +575,15 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
   }
 }
 
-template <int NV, int K, int LIM, int AXIS, bool REC = false>
-__global__ void __launch_bounds__(FaceTile<NV, K, AXIS>::THREADS)
+/* FUSE (x sweep only): tiles of FX_FACES faces overlap by one face, so that a tile holds
+   both faces of FX_FACES - 1 cells; after the faces, the tile differences them in shared
+   memory, adds the other axes' flux differences (their sweeps ran before) and applies the
+   stage combine, writing the stage output: the x faces never go to HBM and no separate
+   cell-update pass runs.  One x face in FX_FACES - 1 is computed twice. */
+template <int NV, int K, int LIM, int AXIS, bool REC = false, bool STATS = false, bool FUSE = false>
+__global__ void __launch_bounds__(FaceTile<NV, K, AXIS>::THREADS, FACE_CTAS_PER_SM)
 face_kernel(const FaceArgs A) {
+  static_assert(!FUSE || (AXIS == 0 && !REC && !STATS), "the cell update is fused into the x sweep only");
   using T = FaceTile<NV, K, AXIS>;
   constexpr int H = T::H;
   extern __shared__ double sm[];
@@ -534,7 +596,7 @@ face_kernel(const FaceArgs A) {
     const int row = blockIdx.x;          /* y + ny * z */
     o1 = row % A.n[1];
     o2 = row / A.n[1];
-    f0 = blockIdx.y * T::FACES;
+    f0 = blockIdx.y * (FUSE ? T::FACES - 1 : T::FACES);
   } else {
     x0 = blockIdx.x * 32;
     f0 = blockIdx.y * T::FACES;
@@ -580,19 +642,60 @@ face_kernel(const FaceArgs A) {
   const int xg = x0 + lane;
   bool active = (f <= na) && (AXIS == 0 || xg < A.n[0]);
   const unsigned am = __ballot_sync(0xffffffffu, active);  /* the lanes sharing the warp's queue */
+  unsigned cnt[STATS ? SC_COUNT : 1];
+#pragma unroll
+  for (int q = 0; q < (STATS ? SC_COUNT : 1); ++q) cnt[q] = 0u;
+  double Fh[NV];
   if (active) {
     /* face linear index (n_a + 1 entries along the axis) */
     long long flin;
     if (AXIS == 0) flin = f + (long long)(A.n[0] + 1) * (o1 + (long long)A.n[1] * o2);
     else if (AXIS == 1) flin = xg + (long long)A.n[0] * (f + (long long)(A.n[1] + 1) * o2);
     else flin = xg + (long long)A.n[0] * (o2 + (long long)A.n[1] * f);
-    double Fh[NV];
-    face_flux_smem<NV, K, LIM, AXIS, T::LANES, REC>(sm, T::NP, jf, lane, A.gamma, A.sch, Fh,
-                                                    A.flags ? A.flags + flin * NV * 2 : nullptr, st,
-                                                    REC ? A.lin + flin : nullptr, A.nface,
-                                                    sm + T::NC * T::NP + (size_t)(tid >> 5) * QSLOTS * (K + 2), am);
+    face_flux_smem<NV, K, LIM, AXIS, T::LANES, REC, STATS>(
+        sm, T::NP, jf, lane, A.gamma, A.sch, Fh, A.flags ? A.flags + flin * NV * 2 : nullptr, st,
+        REC ? A.lin + flin : nullptr, A.nface, sm + T::NC * T::NP + (size_t)(tid >> 5) * QSLOTS * (K + 2), am,
+        cnt);
+    if constexpr (!STATS && !FUSE) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) A.Fhat[v * A.nface + flin] = Fh[v];
+      for (int v = 0; v < NV; ++v) A.Fhat[v * A.nface + flin] = Fh[v];
+    }
+  }
+  if constexpr (FUSE) {
+    /* the tile's faces through shared memory (the point tile is no longer read), then one
+       thread per cell whose two x faces the tile holds */
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) sm[v * T::FACES + tid] = Fh[v];
+    }
+    __syncthreads();
+    const int cx = f0 + tid;
+    if (tid < T::FACES - 1 && cx < A.n[0]) {
+      const long long nc = A.ncell;
+      const long long yz = o1 + (long long)A.n[1] * o2;
+      const long long c = cx + (long long)A.n[0] * yz;
+      double dfx[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) dfx[v] = sm[v * T::FACES + tid + 1] - sm[v * T::FACES + tid];
+      long long fl[3] = {0, 0, 0}, fs[3] = {0, 0, 0};
+      if (NV > 3) {
+        fl[1] = cx + (long long)A.n[0] * (o1 + (long long)(A.n[1] + 1) * o2);
+        fs[1] = A.n[0];
+      }
+      if (NV > 4) {
+        fl[2] = c;
+        fs[2] = (long long)A.n[0] * A.n[1];
+      }
+      cell_update<NV>(A.cu, nc, c, dfx, fl, fs, A.cu.mode != 0 ? *A.cu.dt : 0.0);
+    }
+  }
+  if constexpr (STATS) {  /* warp sums, one 64-bit atomic per counter and warp */
+#pragma unroll
+    for (int q = 0; q < SC_COUNT; ++q) {
+      const unsigned w = __reduce_add_sync(0xffffffffu, cnt[q]);
+      if ((tid & 31) == 0 && w) atomicAdd(A.stats + q, (unsigned long long)w);
+    }
   }
   if (st) atomicOr(A.status, st);
 }

@@ -1,0 +1,11 @@
+/* Decision-statistics face-kernel instantiations for nvar = 3 (1D Euler): the face
+ * kernel's characteristic sequences, counted instead of reconstructed (tenom_stats.cuh). */
+#include "tenom_launch.cuh"
+
+namespace tenom {
+
+cudaError_t launch_stats_nv3(const FaceArgs& a, int axis, int K, int lim, cudaStream_t st) {
+  return launch_face_nv<3, false, true>(a, axis, K, lim, st);
+}
+
+}  // namespace tenom

@@ -198,7 +198,7 @@ __device__ __forceinline__ double va_flux(const double* v) {
 
 /* Adaptive C_T of TENO8A (Section 2.4); returns C_T and [beta] in *e. */
 template <int c>
-__device__ __forceinline__ double adaptive_ct(const double* D, int* e) {
+__device__ __forceinline__ double adaptive_ct(const double* D, int* e, double* beta_out = nullptr) {
   const double xi = 1e-3, Cr = 0.23, a1 = 10.5, a2 = 3.5;
   const double eps = 0.9 * Cr / (1.0 - 0.9 * Cr) * xi * xi;
   double eh = 0.0;
@@ -213,6 +213,7 @@ __device__ __forceinline__ double adaptive_ct(const double* D, int* e) {
   const double om = 1.0 - m;
   const double g = om * om * om * om * (1.0 + 4.0 * m);
   const double beta = a1 - a2 * (1.0 - g);
+  if (beta_out) *beta_out = beta;
   int ex = (int)floor(beta);
   ex = ex < 7 ? 7 : (ex > 10 ? 10 : ex);
   *e = ex;
@@ -228,7 +229,8 @@ __device__ __forceinline__ double adaptive_ct(const double* D, int* e) {
    difference below the FP32 normal range becomes 0, an absolute error far below the
    bound); C = 64 u covers n <= 7 with room.  The bounds are carried
    through tau, gamma_k = (1 + tau/beta_k)^6 (scaled by the largest gamma to stay in range)
-   and the comparison gamma_k < C_T sum gamma.  A decision is returned only when the whole
+   and the comparison gamma_k < C_T sum gamma (quotients by the fast division, whose 2-ulp
+   error the bounds include).  A decision is returned only when the whole
    interval lies on one side; otherwise (and for out-of-range data or an indicator that may
    vanish, where epsilon = 1e-40 matters) the caller decides in FP64.  Certified decisions
    equal the exact-arithmetic decisions, hence those of the FP64 path except where that
@@ -283,13 +285,16 @@ __device__ __forceinline__ bool cutoff_filter(const double (&D)[K - 1], const Sc
       xl[k] = 1.f;
       xh[k] = 1.f;
     } else {
-      xl[k] = (1.f + (tl / bh) * (1.f - 3.f * u)) * (1.f - u);
-      xh[k] = (1.f + (th / bl) * (1.f + 3.f * u)) * (1.f + u);
+      /* fast division: within 2 ulp (relative 4u) for divisors in [2^-126, 2^126] (here
+         bl >= 1e-30 and, with |D| <= 1e15, bh < 1e33), hence 7u where a correctly rounded
+         quotient needed 3u; an overflowing xh fails the range test below */
+      xl[k] = (1.f + __fdividef(tl, bh) * (1.f - 7.f * u)) * (1.f - u);
+      xh[k] = (1.f + __fdividef(th, bl) * (1.f + 7.f * u)) * (1.f + u);
       if (!(xh[k] < 1e30f)) return false;
     }
     xm = fmaxf(xm, xh[k]);
   }
-  const float rxm = 1.f / xm;
+  const float rxm = __fdividef(1.f, xm);  /* a common scale of every gamma: its rounding cancels */
   float gl[nk], gh[nk], Sl = 0.f, Sh = 0.f;
 #pragma unroll
   for (int k = 0; k < nk; ++k) {
@@ -311,10 +316,10 @@ __device__ __forceinline__ bool cutoff_filter(const double (&D)[K - 1], const Sc
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const float dfp = d[c + q - 1], dfm = d[c + q - 2];
-      const float eta = (fabsf(2.f * dfp * dfm) + eps) / (dfp * dfp + dfm * dfm + eps);
+      const float eta = __fdividef(fabsf(2.f * dfp * dfm) + eps, dfp * dfp + dfm * dfm + eps);
       eh = (q == 0) ? eta : fminf(eh, eta);
     }
-    const float m = 1.f - fminf(1.f, eh / Cr);
+    const float m = 1.f - fminf(1.f, eh * (1.f / Cr));
     const float om = 1.f - m;
     const float g = om * om * om * om * (1.f + 4.f * m);
     const float beta = a1 - a2 * (1.f - g);

@@ -21,6 +21,20 @@ CT_CONST, CT_ADAPTIVE = 0, 1
 CURV_M4, CURV_MM = 0, 1
 W_TENOM, W_TENO = 0, 1
 ST_RHO, ST_P, ST_ROE, ST_NONFINITE = 1, 2, 4, 8
+NSTATS = 20  # tenom_decision_stats counters
+STATS_FIELDS = ("sides", "certified", "certified_disagree", "all_smooth", "nonsmooth_k0", "nonsmooth_k1",
+                "nonsmooth_k2", "nonsmooth_k3", "nonsmooth_k4", "nonsmooth_k5", "limited_sides",
+                "limiter_changed", "near_cutoff", "near_cutoff_sides", "ct_exp_7", "ct_exp_8", "ct_exp_9",
+                "ct_exp_10", "near_integer_beta", "nonfinite")
+
+
+def stats_dict(counters, K):
+    """The counters of tenom_decision_stats as a dict (nonsmooth_k for k < K - 2 only)."""
+    vals = [int(x) for x in counters]
+    d = dict(zip(STATS_FIELDS, vals))
+    for k in range(K - 2, 6):
+        d.pop("nonsmooth_k%d" % k)
+    return d
 
 
 class tenom_grid(ctypes.Structure):
@@ -66,6 +80,7 @@ def lib():
         L.tenom_advance.argtypes = [VP, VP, VP, c_double, c_double, c_int]
         L.tenom_advance_host.argtypes = [VP, VP, VP, P(c_double), c_double, c_double, c_int]
         L.tenom_face_dump.argtypes = [VP, VP, c_int, VP, VP]
+        L.tenom_decision_stats.argtypes = [VP, VP, c_int, VP]
         L.tenom_positivity_limit.argtypes = [VP, VP, c_int, VP, VP]
         L.tenom_status_word.argtypes = [VP, P(c_int), c_int]
         L.tenom_last_error.argtypes = [VP]
@@ -111,7 +126,8 @@ def lib():
         L.tenom_rhs_noalloc.restype = c_int
         for name in ("tenom_scheme_default", "tenom_create", "tenom_destroy", "tenom_init_state", "tenom_rhs",
                      "tenom_max_dt", "tenom_rk3_step", "tenom_advance", "tenom_advance_host", "tenom_face_dump",
-                     "tenom_positivity_limit", "tenom_status_word", "tenom_kernel_timing", "tenom_fp64_peak"):
+                     "tenom_positivity_limit", "tenom_status_word", "tenom_kernel_timing", "tenom_fp64_peak",
+                     "tenom_decision_stats"):
             getattr(L, name).restype = c_int
         _lib = L
     return _lib
@@ -347,6 +363,16 @@ class Solver:
         self._check(st, "tenom_rk3_step_adjoint")
         return out
 
+    def decision_stats(self, U, axis, counters=None):
+        """Decision statistics of the reconstruction at U on the faces of one axis: adds
+        the NSTATS counters (tenom_decision_stats) to `counters` (int64 CUDA tensor, made
+        zero if None) and returns it."""
+        import torch
+        if counters is None:
+            counters = torch.zeros(NSTATS, dtype=torch.int64, device="cuda")
+        self._check(lib().tenom_decision_stats(self._ctx, _ptr(U), axis, _ptr(counters)), "tenom_decision_stats")
+        return counters
+
     def status(self, reset=False):
         v = ctypes.c_int(0)
         st = lib().tenom_status_word(self._ctx, ctypes.byref(v), 1 if reset else 0)
@@ -443,6 +469,16 @@ class Batch:
 
     def set_tiling(self, tile, ctas_per_sm):
         self._check(lib().tenom_batch_set_tiling(self._b, tile, ctas_per_sm), "set_tiling")
+
+    def decision_stats(self, U, axis, counters=None):
+        """Decision statistics of the reconstruction at U on the faces of one axis: adds
+        the NSTATS counters (tenom_decision_stats) to `counters` (int64 CUDA tensor, made
+        zero if None) and returns it."""
+        import torch
+        if counters is None:
+            counters = torch.zeros(NSTATS, dtype=torch.int64, device="cuda")
+        self._check(lib().tenom_decision_stats(self._ctx, _ptr(U), axis, _ptr(counters)), "tenom_decision_stats")
+        return counters
 
     def status(self, reset=False):
         v = ctypes.c_int(0)

@@ -26,10 +26,12 @@ def test_batch_config_counts_the_cells_and_flushes_l2():
         assert "flushed" in c["l2"]
 
 
-def test_launch_count_matches_the_committed_launch_lists():
-    """The ncu launch lists under profiles/ (2D 2048^2 TENO6-MP, 6 RK3 steps in the process:
-    3 warm-up, 1 timed, 2 end-to-end) count 90 solver launches without the limiter (face
-    2 x 18, primitives 18, update 18, signal speed, dt and time update 6 each) and 126 with
-    it (plus 2 x 18 limiter passes): 15 and 21 per step."""
-    assert 6 * bench.launches_per_step(2, False) == 36 + 18 + 18 + 6 + 6 + 6
+def test_launch_count_per_step():
+    """Launches of one SSP-RK3 step: signal speed, dt and time update, then per stage the
+    primitives and one sweep per axis (the x sweep carries the cell update): 12 per step
+    in 2D, 15 in 3D; with the positivity limiter per stage also a limiter pass per axis
+    and a separate cell update: 21 in 2D (as the committed limited launch list counts:
+    126 solver launches over 6 steps)."""
+    assert bench.launches_per_step(2, False) == 3 + 3 * 3
+    assert bench.launches_per_step(3, False) == 3 + 3 * 4
     assert 6 * bench.launches_per_step(2, True) == 36 + 36 + 18 + 18 + 6 + 6 + 6

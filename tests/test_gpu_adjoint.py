@@ -222,10 +222,12 @@ def test_rollout_gradient_wrt_initial_density_vs_central_differences(T):
     circular jumps (64^2), TENO6-MP, 20 steps at fixed dt, loss = integral of p over a
     16 x 16 window, gradient with respect to the initial density (u, v, p fixed) through
     torch.autograd with checkpoints every 5 steps.  Over 20 steps the forward crosses
-    branch switches (cutoff, limiter, LLF argmax) at any difference step large enough to
-    beat rounding, so central differences (step 1e-8) agree only to their floor (measured
-    2e-5 .. 1.2e-4 on this field); the bound is 1e-3.  Exactness is established by the
-    dual-number identities and the per-cell checks above."""
+    branch switches (cutoff, limiter, LLF argmax): on this field a decision lies within
+    about 3e-8 of its switch along most directions, so central differences at steps of
+    3e-8 and above carry a jump (errors 2e-3 .. 7e-2 of |grad|), while at 1e-8 these four
+    directions stay on one side and agree to their rounding floor (measured 3e-7 .. 9e-7 of
+    |grad|); the bound is three times that.  Exactness is established by the dual-number
+    identities and the per-cell checks above."""
     from paper_2010_13289_gb300.autograd import rollout
     n, steps, gam = 64, 20, 1.4
     prim, dx = PB.broadband_2d(n, 5, kmax=8)
@@ -261,4 +263,4 @@ def test_rollout_gradient_wrt_initial_density_vs_central_differences(T):
         ad = float((grad_rho * d).sum())
         # unit directions: the error is measured against the gradient norm (a direction
         # nearly orthogonal to the gradient has a derivative below the FD rounding floor)
-        assert abs(fd - ad) <= 1e-3 * gnorm, (k, fd, ad, gnorm)
+        assert abs(fd - ad) <= 3e-6 * gnorm, (k, fd, ad, gnorm)

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 from paper_2010_13289_gb300 import problems as PB
-from parity import compare_faces, compare_rhs, switch_cells
+from parity import CUT_TOL, NOISE_K, bound_counts, compare_cells, compare_faces, compare_rhs, dilate, switch_cells
 
 pytestmark = pytest.mark.gpu
 
@@ -69,8 +69,9 @@ def test_face_flux_parity(T, orc, shape, bc, K, lim, jumps):
         st = compare_faces(Fg.cpu().numpy(), flg.cpu().numpy(), Fo, flo, cut, noise, scale,
                            label="%s axis %d" % (shape, a))
         # near-cutoff switches are rare; noise-decided ones sit where a characteristic field
-        # is flat to rounding (transmissive ghost copies, degenerate fields)
-        assert st["near_cutoff_faces"] <= max(2, 0.01 * st["faces"]), st
+        # is flat to rounding (transmissive ghost copies, the acoustic fields across a
+        # contact): up to 4 % of the faces on the small 3D grids with transmissive axes
+        bound_counts(st, noise_frac=0.05)
         Fs.append(Fo)
         sw.append((flg.cpu().numpy() != flo).reshape(flo.shape[:-2] + (-1,)).any(axis=-1))
     ro, _ = orc.rhs(g, so, Uo)
@@ -87,7 +88,7 @@ def face_parity_checks(T, orc, S, g, so, Uo, Ug, shape):
         assert bad == 0
         st = compare_faces(Fg.cpu().numpy(), flg.cpu().numpy(), Fo, flo, cut, noise, scale,
                            label="%s axis %d" % (shape, a))
-        assert st["near_cutoff_faces"] <= max(2, 0.01 * st["faces"]), st
+        bound_counts(st, noise_frac=0.05)
     assert S.status() == 0
 
 
@@ -121,6 +122,30 @@ def test_face_flux_parity_scheme_variants(T, orc, shape, bc, K, lim, kw):
     S.close()
 
 
+def step_switch_region(T, orc, S, g, so, Uo, dto, shape, K, label):
+    """Cells that a cutoff decision set by rounding can reach within one SSP-RK3 step: at
+    each stage state (the oracle's), the faces whose GPU and oracle flags differ (each
+    such difference is checked to be near the cutoff or noise-decided, and counted), their
+    neighbour cells, dilated by two stencil half-widths plus one cell per later stage."""
+    L0, _ = orc.rhs(g, so, Uo)
+    U1 = Uo + dto * L0
+    L1, _ = orc.rhs(g, so, U1)
+    U2 = 0.75 * Uo + 0.25 * (U1 + dto * L1)
+    region = np.zeros(Uo.shape[1:], dtype=bool)
+    for st_i, X in enumerate((Uo, U1, U2)):
+        Xg = torch.from_numpy(np.ascontiguousarray(X)).cuda()
+        sw = []
+        for a in range(len(shape)):
+            Fg, flg = S.face_dump(Xg, a)
+            Fo, flo, cut, noise, bad, scale = orc.faces(g, so, X, a, with_scale=True)
+            st = compare_faces(Fg.cpu().numpy(), flg.cpu().numpy(), Fo, flo, cut, noise, scale,
+                               label="%s stage %d axis %d" % (label, st_i + 1, a))
+            bound_counts(st)
+            sw.append((flg.cpu().numpy() != flo).reshape(flo.shape[:-2] + (-1,)).any(axis=-1))
+        region |= dilate(switch_cells(sw, Uo.shape[1:]), K + 3 - st_i)
+    return region
+
+
 def test_van_albada_steps_match_and_adjoint_is_refused(T, orc):
     """TENO-M-VA through SSP-RK3 steps agrees with the oracle; its adjoint is reported as
     not supported (the Van Albada flux is not a selection among linear forms)."""
@@ -131,8 +156,9 @@ def test_van_albada_steps_match_and_adjoint_is_refused(T, orc):
     dt = torch.tensor([dto], dtype=torch.float64, device="cuda")
     U1o, _ = orc.rk3_step(g, so, Uo, dto)
     U1g = S.rk3_step(Ug.clone(), dt).cpu().numpy()
-    err = np.abs(U1g - U1o) / np.maximum(np.abs(U1o), 1e-3 * np.abs(U1o).max(axis=(1, 2), keepdims=True))
-    assert float(np.mean(err > 1e-12)) < 0.01 and np.median(err) < 1e-15
+    ex = step_switch_region(T, orc, S, g, so, Uo, dto, shape, 6, "VA step")
+    assert float(ex.mean()) < 0.1, float(ex.mean())
+    compare_cells(U1g, U1o, exclude=ex, rel=1e-13, label="VA step")
     with pytest.raises(T.TenomError) as ei:
         S.rhs_vjp(Ug, Ug.clone())
     assert ei.value.status == T.TENOM_E_UNSUPPORTED
@@ -154,11 +180,11 @@ def test_rk3_step_and_max_dt_parity(T, orc, K, lim):
     dt = torch.tensor([dto], dtype=torch.float64, device="cuda")
     U1o, _ = orc.rk3_step(g, so, Uo, dto)
     U1g = S.rk3_step(Ug.clone(), dt).cpu().numpy()
-    err = np.abs(U1g - U1o) / np.maximum(np.abs(U1o), 1e-3 * np.abs(U1o).max(axis=(1, 2), keepdims=True))
-    # a rare cutoff switch changes a few cells by more; everything else agrees to 1e-12
-    frac_bad = float(np.mean(err > 1e-12))
-    assert frac_bad < 0.01, (frac_bad, err.max())
-    assert np.median(err) < 1e-15
+    # cells within reach of a rounding-decided cutoff switch are set aside (counted, at most
+    # a tenth of the grid); every other cell agrees to 1e-13
+    ex = step_switch_region(T, orc, S, g, so, Uo, dto, shape, K, "rk3 K=%d lim=%d" % (K, lim))
+    assert float(ex.mean()) < 0.1, float(ex.mean())
+    compare_cells(U1g, U1o, exclude=ex, rel=1e-13, label="rk3 step K=%d lim=%d" % (K, lim))
 
 
 def c1_oracle_run(orc, n=256, seed=1, K=6, lim=0):
@@ -215,7 +241,9 @@ def test_degenerate_sizes(T, orc, shape, bc, K):
     for a in range(len(shape)):
         Fg, flg = S.face_dump(Ug, a)
         Fo, flo, cut, noise, bad, scale = orc.faces(g, so, Uo, a, with_scale=True)
-        compare_faces(Fg.cpu().numpy(), flg.cpu().numpy(), Fo, flo, cut, noise, scale, label="%s" % (shape,))
+        st = compare_faces(Fg.cpu().numpy(), flg.cpu().numpy(), Fo, flo, cut, noise, scale,
+                           label="degenerate %s axis %d" % (shape, a))
+        bound_counts(st)
 
 
 def test_invalid_arguments_rejected(T):
@@ -256,7 +284,7 @@ def sample_faces(rng, shape, axis, m):
     return idx
 
 
-def check_sampled(T, orc, S, g, so, Ug, Uo, shape, m, seed):
+def check_sampled(T, orc, S, g, so, Ug, Uo, shape, m, seed, label="", smooth=False):
     rng = np.random.default_rng(seed)
     for a in range(len(shape)):
         Fg, flg = S.face_dump(Ug, a)
@@ -266,7 +294,10 @@ def check_sampled(T, orc, S, g, so, Ug, Uo, shape, m, seed):
         Fo, flo, cut, noise, bad, scale = orc.faces_at(g, so, Uo, a, idx, with_scale=True)
         sel = tuple(idx[:, d] for d in reversed(range(len(shape))))
         Fgs = np.stack([Fg[v][sel] for v in range(len(shape) + 2)])
-        compare_faces(Fgs, flg[sel], Fo.T, flo, cut, noise, scale.T, label="sampled axis %d" % a)
+        st = compare_faces(Fgs, flg[sel], Fo.T, flo, cut, noise, scale.T, label="%s sampled axis %d" % (label, a))
+        bound_counts(st)
+        if smooth:  # no characteristic field of these smooth-plus-jump fields is flat to rounding
+            assert st["noise_faces"] == 0, st
         # the face fluxes of all faces must be finite
         assert np.isfinite(Fg).all()
         del Fg, flg
@@ -278,7 +309,8 @@ def test_full_size_2d_sampled(T, orc):
     prim, dx = PB.broadband_2d(2048, 2)
     for K, lim in ((6, 0), (8, 1)):
         S, g, so, Uo, Ug = setup(T, orc, (2048, 2048), (0, 0), K, lim, prim, dx=(dx, dx))
-        check_sampled(T, orc, S, g, so, Ug, Uo, (2048, 2048), 4000, K)
+        check_sampled(T, orc, S, g, so, Ug, Uo, (2048, 2048), 4000, K, label="broadband 2048^2 K=%d" % K,
+                      smooth=True)
         S.close()
 
 
@@ -287,7 +319,7 @@ def test_full_size_3d_sampled(T, orc):
     prim, dx = PB.solenoidal_3d(256, 3)
     S, g, so, Uo, Ug = setup(T, orc, (256, 256, 256), (0, 0, 0), 8, 0, prim, dx=(dx, dx, dx))
     del prim
-    check_sampled(T, orc, S, g, so, Ug, Uo, (256, 256, 256), 3000, 3)
+    check_sampled(T, orc, S, g, so, Ug, Uo, (256, 256, 256), 3000, 3, label="solenoidal 256^3", smooth=True)
 
 
 FILTER_CASES = [
@@ -338,7 +370,12 @@ def test_taylor_green_parity_and_conservation(T, orc):
         Fg, flg = S.face_dump(Ug, a)
         Fo, flo, cut, noise, bad, scale = orc.faces(g, so, Uo, a, with_scale=True)
         assert bad == 0
-        compare_faces(Fg.cpu().numpy(), flg.cpu().numpy(), Fo, flo, cut, noise, scale, label="TGV axis %d" % a)
+        # the symmetric field makes face values vanish exactly on its symmetry planes, where
+        # both sides return rounding noise of terms that cancel before the back-projection:
+        # these faces are measured against 1e-3 of the component's largest value
+        st = compare_faces(Fg.cpu().numpy(), flg.cpu().numpy(), Fo, flo, cut, noise, scale, label="TGV axis %d" % a,
+                           floor=True)
+        bound_counts(st, noise_frac=0.1, floor=True)
     dt = S.max_dt(Ug, 0.4)
     U = Ug.clone()
     ke = lambda X: float((0.5 * (X[1] ** 2 + X[2] ** 2 + X[3] ** 2) / X[0]).sum())
@@ -349,3 +386,52 @@ def test_taylor_green_parity_and_conservation(T, orc):
     assert float(((U.sum(dim=(1, 2, 3)) - tot0).abs() / scale).max()) < 1e-13
     assert ke(U) <= ke0 * (1 + 1e-3)
     assert S.status() == 0
+
+
+STATS_CASES = [((70, 45), (0, 0), 6, 0), ((70, 45), (1, 0), 8, 1), ((20, 13, 11), (0, 0, 1), 8, 0),
+               ((300,), (1,), 6, 0), ((64, 48), (0, 0), 6, 2)]
+
+
+@pytest.mark.parametrize("shape,bc,K,lim", STATS_CASES)
+def test_decision_stats_match_oracle(T, orc, shape, bc, K, lim):
+    """The logging pass (tenom_decision_stats) counts what the oracle decides: per split side
+    the nonsmooth candidates per k (Eq. cut-off), the all-smooth sides, the adaptive [beta]
+    histogram (Eq. cut-off_adjust) and the near-cutoff sides, equal to the oracle's counts
+    up to the sides whose decision the parity rules excuse (near the cutoff or set by
+    rounding); the limiter's sides and changes are consistent with them."""
+    prim = PB.random_state(tuple(reversed(shape)), seed=sum(shape) + 11 * K + lim, jumps=True)
+    S, g, so, Uo, Ug = setup(T, orc, shape, bc, K, lim, prim)
+    for a in range(len(shape)):
+        cnt = S.decision_stats(Ug, a)
+        c = T.stats_dict(cnt.cpu().numpy(), K)
+        Fo, flo, cut, noise, bad, scale = orc.faces(g, so, Uo, a, with_scale=True)
+        fl = flo.reshape(-1).astype(np.int64)
+        cu, no = cut.reshape(-1), noise.reshape(-1)
+        excused = int(((cu <= CUT_TOL) | (cu <= NOISE_K * no)).sum())
+        assert c["sides"] == fl.size
+        bits = fl & 63
+        total_ns = 0
+        for k in range(K - 2):
+            o = int((((bits >> k) & 1) == 0).sum())
+            assert abs(c["nonsmooth_k%d" % k] - o) <= excused, (k, c, o, excused)
+            total_ns += c["nonsmooth_k%d" % k]
+        assert total_ns > 0  # the jumps make some candidates nonsmooth
+        allsm = int((bits == (1 << (K - 2)) - 1).sum())
+        assert abs(c["all_smooth"] - allsm) <= excused, (c, allsm)
+        assert c["limited_sides"] == c["sides"] - c["all_smooth"]
+        assert 0 < c["limiter_changed"] <= total_ns
+        assert c["certified"] > 0.25 * c["sides"] and c["certified_disagree"] <= excused
+        if K == 8:
+            hist = [int((((fl >> 6) & 3) == j).sum()) for j in range(4)]
+            for j in range(4):
+                assert abs(c["ct_exp_%d" % (7 + j)] - hist[j]) <= excused, (c, hist)
+        near = int((cu <= CUT_TOL).sum())
+        assert abs(c["near_cutoff_sides"] + c["near_integer_beta"] - near) <= 1 + near, (c, near)
+        assert c["nonfinite"] == 0
+    # the counters add up over calls
+    cnt = S.decision_stats(Ug, 0)
+    S.decision_stats(Ug, 0, counters=cnt)
+    c2 = T.stats_dict(cnt.cpu().numpy(), K)
+    c1 = T.stats_dict(S.decision_stats(Ug, 0).cpu().numpy(), K)
+    assert all(c2[k] == 2 * c1[k] for k in c1)
+    S.close()

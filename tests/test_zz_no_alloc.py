@@ -63,3 +63,31 @@ def test_noalloc_rejects_grid_beyond_scratch(T):
     st = T.lib().tenom_rhs_noalloc(ctypes.byref(grid), ctypes.byref(scheme), _p(U), _p(out), None, None)
     assert st == T.TENOM_E_INVALID
     assert float(out.abs().max()) == 0.0  # nothing was launched
+
+
+def test_noalloc_status_word(T):
+    """A cell with negative pressure must set the pressure bit (TENOM_ST_P) in the caller's status word, and a
+    call with no status word (NULL) on a valid state must still return the operator."""
+    shape, bc = (64, 48), (0, 0)
+    dx = (1.0 / 64, 1.0 / 48)
+    scheme = T.make_scheme(6)
+    grid = T.make_grid(shape, dx, bc)
+    S = T.Solver(shape, dx, bc, scheme)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    prim = PB.random_state(tuple(reversed(shape)), 3, jumps=True)
+    U = S.init_state(torch.from_numpy(prim).cuda())
+    want = S.rhs(U)
+    got = torch.full_like(want, float("nan"))
+    st = T.lib().tenom_rhs_noalloc(ctypes.byref(grid), ctypes.byref(scheme), _p(U), _p(got), None, stream)
+    assert st == T.TENOM_OK
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(got.cpu().numpy(), want.cpu().numpy(), rtol=1e-13, atol=1e-13)
+
+    bad = U.clone()
+    bad[3, 10, 20] = 0.5 * (bad[1, 10, 20] ** 2 + bad[2, 10, 20] ** 2) / bad[0, 10, 20] - 1.0  # p < 0
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = T.lib().tenom_rhs_noalloc(ctypes.byref(grid), ctypes.byref(scheme), _p(bad), _p(got), _p(status), stream)
+    assert st == T.TENOM_OK
+    torch.cuda.synchronize()
+    assert status.item() & T.ST_P
+    S.close()
