@@ -34,6 +34,10 @@ WORKLOADS = {
     "solenoidal_3d_256_teno8_mp": ("solenoidal_3d", (256, 256, 256), 8, 0),
     # a smaller case of the same 3D field recipe, for ncu captures (0.5 GB on the device)
     "solenoidal_3d_128_teno8_mp": ("solenoidal_3d", (128, 128, 128), 8, 0),
+    # slabs of the 256^3 field for ncu captures of its face kernels: 32 planes thin in z
+    # (the x and y sweeps see exactly the full field's stencils) or thin in y (the z sweep)
+    "solenoidal_3d_256_slab_z32_teno8_mp": ("solenoidal_3d_slab_z", (256, 256, 32), 8, 0),
+    "solenoidal_3d_256_slab_y32_teno8_mp": ("solenoidal_3d_slab_y", (256, 32, 256), 8, 0),
 }
 BATCH_WORKLOADS = {
     # name: (problems, seed, nmin, nmax, K, limiter)
@@ -102,11 +106,18 @@ def flops_per_face(name):
 
 
 def make_prim(name, seed):
+    import numpy as np
     from paper_2010_13289_gb300 import problems as PB
     gen, shape, K, lim = WORKLOADS[name]
     if gen == "broadband_2d":
         prim, dx = PB.broadband_2d(shape[0], seed)
         return prim, (dx, dx)
+    if gen == "solenoidal_3d_slab_z":
+        prim, dx = PB.solenoidal_3d(256, seed)
+        return np.ascontiguousarray(prim[:, :shape[2]]), (dx, dx, dx)
+    if gen == "solenoidal_3d_slab_y":
+        prim, dx = PB.solenoidal_3d(256, seed)
+        return np.ascontiguousarray(prim[:, :, :shape[1]]), (dx, dx, dx)
     prim, dx = PB.solenoidal_3d(shape[0], seed)
     return prim, (dx, dx, dx)
 
@@ -297,12 +308,9 @@ def oracle_rate_batch(name, seconds):
 
 def launches_per_step(dim, positivity):
     """Kernel launches of one SSP-RK3 step of a grid workload: the signal-speed reduction, dt
-    and the time update, and per stage the primitives and one face sweep per axis, the x
-    sweep carrying the cell update; with the positivity limiter, per stage also one limiter
-    pass per axis and a separate cell-update pass."""
-    if positivity:
-        return 3 + 3 * (2 * dim + 2)
-    return 3 + 3 * (dim + 1)
+    and the time update, and per stage the primitives, one face sweep per axis (plus one
+    limiter pass per axis when the positivity limiter is on) and the cell update."""
+    return 3 + 3 * (dim * (2 if positivity else 1) + 2)
 
 
 def grid_config(name, ws, positivity):

@@ -223,8 +223,9 @@ tenom_status tenom_batch_set_tiling(tenom_batch* b, int tile, int ctas_per_sm);
  * and flux-difference kernels of tenom_rhs.  One difference: tenom_rhs first computes the
  * cells' primitives (velocity, p, H, c, sqrt rho) once per cell into its context's
  * buffer, while this call has no such buffer and the face kernels form them for each
- * staged point of their tile; the two orders of evaluation round alike except in the last
- * bits (agreement to 1e-13 relative is tested).  U and dUdt are caller-owned device arrays as for tenom_rhs; status_dev
+ * staged point of their tile; the two round alike except in the last bits, which can
+ * flip a cutoff decision that rounding sets (a flat sequence at a zero-gradient boundary);
+ * agreement to 1e-13 of each component's largest value is tested.  U and dUdt are caller-owned device arrays as for tenom_rhs; status_dev
  * is an optional caller-owned device int that receives TENOM_ST_* bits (ORed in, the
  * caller clears it); with NULL the bits go to a word inside the scratch and are not
  * reported.

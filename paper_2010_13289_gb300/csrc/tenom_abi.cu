@@ -35,6 +35,49 @@ __global__ void init_state_kernel(const double* __restrict__ prim, double* __res
   }
 }
 
+/* Flux difference -sum_a (F_{a,i+1/2} - F_{a,i-1/2}) / dx_a (Eq. approximateEq) and the
+   SSP-RK3 stage combine of one cell: mode 0 out = L (operator), 1 out = Us + dt L (stage
+   1), 2 out = cA U0 + cB (Us + dt L) (stages 2, 3); dt = 0 (a step past t_end) keeps Us. */
+struct CellUpdate {
+  const double* F[3];  /* face buffers per axis [NV][nface_a] */
+  const double* U0;    /* U^n (stages 2, 3) */
+  const double* Us;    /* stage input state */
+  double* out;         /* stage output or dU/dt */
+  const double* dt;    /* device dt (null for the operator) */
+  double rdx[3];       /* 1 / dx_a */
+  long long nface[3];
+  double cA, cB;
+  int mode;
+};
+
+/* the cell update of cell c whose x-face difference F_{x,i+1/2} - F_{x,i-1/2} is dfx; the
+   other axes' faces at fl[a] and fl[a] + fs[a] */
+template <int NV>
+__device__ __forceinline__ void cell_update(const CellUpdate& A, long long nc, long long c, const double (&dfx)[NV],
+                                            const long long (&fl)[3], const long long (&fs)[3], double dt) {
+  constexpr int DIM = NV - 2;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    double r = 0.0;
+    r = r - dfx[v] * A.rdx[0];
+#pragma unroll
+    for (int a = 1; a < DIM; ++a) {
+      const double* F = A.F[a] + v * A.nface[a];
+      r = r - (F[fl[a] + fs[a]] - F[fl[a]]) * A.rdx[a];
+    }
+    if (A.mode == 0) {
+      A.out[v * nc + c] = r;
+    } else if (dt == 0.0) {
+      /* a step past t_end: every stage state equals U^n, keep it bit for bit */
+      A.out[v * nc + c] = A.Us[v * nc + c];
+    } else {
+      const double us = A.Us[v * nc + c];
+      const double t1 = us + dt * r;
+      A.out[v * nc + c] = (A.mode == 1) ? t1 : A.cA * A.U0[v * nc + c] + A.cB * t1;
+    }
+  }
+}
+
 struct StageArgs {
   CellUpdate cu;       /* faces of every axis, states, dt, 1/dx_a, stage coefficients */
   int n[3];
@@ -42,8 +85,7 @@ struct StageArgs {
 };
 
 /* Flux difference -sum_a (F_{a,i+1/2} - F_{a,i-1/2})/dx_a (Eq. approximateEq) fused with
-   the SSP-RK3 stage combine (cell_update, shared with the fused x sweep so that both give
-   the same bits); 1/dx_a is formed once on the host (an FP64 division per cell and axis
+   the SSP-RK3 stage combine (cell_update); 1/dx_a is formed once on the host (an FP64 division per cell and axis
    would occupy the FP64 pipe longer than the kernel's memory traffic takes). */
 template <int NV>
 __global__ void stage_kernel(const StageArgs A) {
@@ -325,8 +367,7 @@ struct tenom_ctx {
   int nv;
   long long ncell;
   long long nface[3];
-  double* W1;          /* stage buffers: stage 1 writes W1, stage 2 reads W1 and writes W2 */
-  double* W2;
+  double* W1;          /* stage buffer */
   double* face[3];     /* face buffers */
   double* P;           /* per-cell primitives of the stage being evaluated ([nvar + 2][ncell]) */
   double* dt;          /* device dt */
@@ -461,9 +502,7 @@ tenom_status tenom_create(tenom_ctx** out, const tenom_grid* grid, const tenom_s
   c->ev_used = 0;
   c->face_ms = 0;
   c->face_launches = 0;
-  c->W2 = nullptr;
   cudaError_t e = cudaMalloc(&c->W1, sizeof(double) * c->nv * c->ncell);
-  if (e == cudaSuccess) e = cudaMalloc(&c->W2, sizeof(double) * c->nv * c->ncell);
   for (int a = 0; a < grid->dim && e == cudaSuccess; ++a) e = cudaMalloc(&c->face[a], sizeof(double) * c->nv * c->nface[a]);
   if (e == cudaSuccess) e = cudaMalloc(&c->P, sizeof(double) * (c->nv + 2) * c->ncell);
   if (e == cudaSuccess) e = cudaMalloc(&c->dt, sizeof(double) * 2);
@@ -487,7 +526,6 @@ tenom_status tenom_destroy(tenom_ctx* c) {
   if (!c) return TENOM_OK;
   cudaStreamSynchronize(c->st);
   cudaFree(c->W1);
-  cudaFree(c->W2);
   for (int a = 0; a < 3; ++a) cudaFree(c->face[a]);
   cudaFree(c->P);
   cudaFree(c->dt);
@@ -539,15 +577,12 @@ static FaceArgs face_args(tenom_ctx* c, const double* U, int axis, double* F, ui
   return a;
 }
 
-/* one face sweep of axis `axis` at U (P: its cell primitives); with cu (axis 0 only) the x
-   sweep also applies the cell update (flux difference, stage combine) instead of writing
-   its faces */
+/* one face sweep of axis `axis` at U (P: its cell primitives) */
 static cudaError_t launch_faces(tenom_ctx* c, const double* U, int axis, double* F, uint8_t* flags,
-                                double* lin = nullptr, const double* P = nullptr, const CellUpdate* cu = nullptr) {
+                                double* lin = nullptr, const double* P = nullptr) {
   FaceArgs a = face_args(c, U, axis, F, flags);
   a.lin = lin;
   a.P = P;
-  if (cu) a.cu = *cu;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (c->timing) {
     while (c->ev.size() < c->ev_used + 2) {
@@ -562,11 +597,7 @@ static cudaError_t launch_faces(tenom_ctx* c, const double* U, int axis, double*
     cudaEventRecord(e0, c->st);
   }
   cudaError_t e;
-  if (cu) {
-    if (c->nv == 3) e = launch_fused_nv3(a, c->s.K, c->s.limiter, c->st);
-    else if (c->nv == 4) e = launch_fused_nv4(a, c->s.K, c->s.limiter, c->st);
-    else e = launch_fused_nv5(a, c->s.K, c->s.limiter, c->st);
-  } else if (lin) {
+  if (lin) {
     if (c->nv == 3) e = launch_face_rec_nv3(a, axis, c->s.K, c->s.limiter, c->st);
     else if (c->nv == 4) e = launch_face_rec_nv4(a, axis, c->s.K, c->s.limiter, c->st);
     else e = launch_face_rec_nv5(a, axis, c->s.K, c->s.limiter, c->st);
@@ -624,23 +655,11 @@ static cudaError_t eval_faces(tenom_ctx* c, const double* U) {
   return e;
 }
 
-/* One evaluation of the operator at Us with the cell update fused into the x sweep: the
-   primitives, the sweeps of the other axes (faces to their buffers), then the x sweep,
-   which differences its faces in the tile and writes out = the stage combine of mode
-   (out must not be Us: other tiles still read Us). */
-static cudaError_t fused_stage(tenom_ctx* c, const double* Us, const double* U0, double* out, int mode, double cA,
-                               double cB) {
-  cudaError_t e = launch_prims(c, Us);
-  for (int a = 1; a < c->g.dim && e == cudaSuccess; ++a) e = launch_faces(c, Us, a, c->face[a], nullptr, nullptr, c->P);
-  if (e != cudaSuccess) return e;
-  const CellUpdate cu = cell_update_args(c, U0, Us, out, mode, cA, cB);
-  return launch_faces(c, Us, 0, nullptr, nullptr, nullptr, c->P, &cu);
-}
-
 tenom_status tenom_rhs(tenom_ctx* c, const double* U, double* dUdt) {
   if (!c) return TENOM_E_INVALID;
   if (!aligned8(U) || !aligned8(dUdt) || U == dUdt) return fail(c, TENOM_E_INVALID, "rhs: bad pointers");
-  cudaError_t e = fused_stage(c, U, nullptr, dUdt, 0, 0.0, 0.0);
+  cudaError_t e = eval_faces(c, U);
+  if (e == cudaSuccess) e = launch_stage(c, nullptr, U, dUdt, 0, 0.0, 0.0);
   return e == cudaSuccess ? TENOM_OK : cuda_fail(c, e, "rhs");
 }
 
@@ -698,17 +717,8 @@ static cudaError_t stage_faces(tenom_ctx* c, const double* Us) {
   return e;
 }
 
-/* three stages; dt already in c->dt.  Without the positivity limiter each stage is one
-   fused evaluation (stage 2 writes W2, so that no stage overwrites the state its x sweep
-   reads); the limiter needs every face of the stage before any cell update, so with it the
-   faces go through their buffers and a separate cell-update pass. */
+/* three stages; dt already in c->dt */
 static cudaError_t rk3_core(tenom_ctx* c, double* U) {
-  if (c->s.positivity != TENOM_PP_ON) {
-    cudaError_t e = fused_stage(c, U, nullptr, c->W1, 1, 0.0, 1.0);
-    if (e == cudaSuccess) e = fused_stage(c, c->W1, U, c->W2, 2, 0.75, 0.25);
-    if (e == cudaSuccess) e = fused_stage(c, c->W2, U, U, 2, 1.0 / 3.0, 2.0 / 3.0);
-    return e;
-  }
   cudaError_t e = stage_faces(c, U);
   if (e == cudaSuccess) e = launch_stage(c, nullptr, U, c->W1, 1, 0.0, 1.0);
   if (e == cudaSuccess) e = stage_faces(c, c->W1);

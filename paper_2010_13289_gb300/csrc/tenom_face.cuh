@@ -18,51 +18,10 @@
 #include "tenom_linear.cuh"
 #include "tenom_stats.cuh"
 #include "tenom_fastmath.cuh"
+#include "tenom_queue.cuh"
+#include "tenom_face_fwd.cuh"
 
 namespace tenom {
-
-/* Flux difference -sum_a (F_{a,i+1/2} - F_{a,i-1/2}) / dx_a (Eq. approximateEq) and the
-   SSP-RK3 stage combine of one cell: mode 0 out = L (operator), 1 out = Us + dt L (stage
-   1), 2 out = cA U0 + cB (Us + dt L) (stages 2, 3); dt = 0 (a step past t_end) keeps Us. */
-struct CellUpdate {
-  const double* F[3];  /* face buffers per axis [NV][nface_a] (the fused x sweep reads F[1], F[2]) */
-  const double* U0;    /* U^n (stages 2, 3) */
-  const double* Us;    /* stage input state */
-  double* out;         /* stage output or dU/dt (never Us when fused into the x sweep) */
-  const double* dt;    /* device dt (null for the operator) */
-  double rdx[3];       /* 1 / dx_a */
-  long long nface[3];
-  double cA, cB;
-  int mode;
-};
-
-/* the cell update of cell c whose x-face difference F_{x,i+1/2} - F_{x,i-1/2} is dfx; the
-   other axes' faces at fl[a] and fl[a] + fs[a] */
-template <int NV>
-__device__ __forceinline__ void cell_update(const CellUpdate& A, long long nc, long long c, const double (&dfx)[NV],
-                                            const long long (&fl)[3], const long long (&fs)[3], double dt) {
-  constexpr int DIM = NV - 2;
-#pragma unroll
-  for (int v = 0; v < NV; ++v) {
-    double r = 0.0;
-    r = r - dfx[v] * A.rdx[0];
-#pragma unroll
-    for (int a = 1; a < DIM; ++a) {
-      const double* F = A.F[a] + v * A.nface[a];
-      r = r - (F[fl[a] + fs[a]] - F[fl[a]]) * A.rdx[a];
-    }
-    if (A.mode == 0) {
-      A.out[v * nc + c] = r;
-    } else if (dt == 0.0) {
-      /* a step past t_end: every stage state equals U^n, keep it bit for bit */
-      A.out[v * nc + c] = A.Us[v * nc + c];
-    } else {
-      const double us = A.Us[v * nc + c];
-      const double t1 = us + dt * r;
-      A.out[v * nc + c] = (A.mode == 1) ? t1 : A.cA * A.U0[v * nc + c] + A.cB * t1;
-    }
-  }
-}
 
 struct FaceArgs {
   const double* U;    /* [NV][ncell] */
@@ -78,7 +37,6 @@ struct FaceArgs {
   long long nface;
   double gamma;
   SchemeDev sch;
-  CellUpdate cu;      /* the fused x sweep's cell update (FUSE kernels only) */
 };
 
 /* shared-memory layout of the staged point quantities: component c of point p at c * NP + p */
@@ -94,7 +52,6 @@ constexpr int FX_FACES = 128;  /* faces per CTA, x sweeps */
    the compiler room for ~168 registers (the halo rows cost little once the cell primitives
    come from the per-stage kernel) */
 __host__ __device__ constexpr int ft_faces(int K) { return (void)K, 4; }
-constexpr int QSLOTS = 64;     /* reconstruction queue items per warp: two sides x 32 lanes */
 /* resident CTAs per SM the face kernels are compiled for: 3 x 128 threads leave 168
    registers a thread (K = 8 with the deferred queue spills about 130 bytes a thread to
    local memory at this budget and still runs 8 % faster on the 3D workload than with 214
@@ -114,7 +71,19 @@ struct FaceTile {
   /* + one reconstruction queue per warp (recon_pair_queued) */
   static constexpr size_t QDOUBLES = (size_t)(THREADS / 32) * QSLOTS * (K + 2);
   static constexpr size_t SMEM_Q = SMEM + sizeof(double) * QDOUBLES;
+  /* forward kernels (face_flux_fwd): their point layout, one field queue per warp, then
+     the FP32 copies of the point data */
+  static constexpr int NCF = PointLayoutF<NV>::NC;
+  static constexpr size_t FQDOUBLES = (size_t)(THREADS / 32) * FQCAP * fq_rows<NV>();
+  static constexpr size_t SMEM_FWD =
+      sizeof(double) * ((size_t)NCF * NP + FQDOUBLES) + sizeof(float) * (size_t)PointLayoutF<NV>::NF * NP;
 };
+
+/* dynamic shared memory of face_kernel<..., REC, STATS, ...> */
+template <int NV, int K, int AXIS, bool REC, bool STATS>
+constexpr size_t face_smem() {
+  return (!REC && !STATS) ? FaceTile<NV, K, AXIS>::SMEM_FWD : FaceTile<NV, K, AXIS>::SMEM_Q;
+}
 
 __device__ __forceinline__ int bc_wrap(int j, int n, int bc) {
   if (bc == 0) {
@@ -176,45 +145,6 @@ __device__ __forceinline__ void stage_point(const double (&u)[NV], double gamma,
   double vel[NV - 2], pr, Hh, c, sr;
   point_prims<NV>(u, gamma, vel, pr, Hh, c, sr, st);
   stage_point_from<NV, AXIS>(u, vel, pr, Hh, c, sr, sm, NP, p);
-}
-
-/* Warp work queue for the two reconstructions (f+, f-) of one characteristic field.
- * After the certified FP32 cutoff decisions, a side whose candidates are all smooth takes
- * the K-point central formula in its own lane; every other side (nonsmooth candidates, or
- * decisions the filter could not certify) is queued in shared memory and the warp's
- * active lanes work through the queue together, so the long general path (FP64 decisions,
- * candidates, limiter, assembly) runs with full lanes instead of once per side under
- * divergence.  wq: this warp's queue, QSLOTS items x (K + 2) doubles, component-major
- * (values, result, header); am: the warp's active lanes.  WT: the frozen linear weights
- * of each side (teno_general) come back in wp / wm. */
-/* queue item r: the K stencil values and a header (decided flag bits, or undecided) */
-template <int K>
-__device__ __forceinline__ void queue_put(double* wq, int r, const double (&v)[K], bool decided, unsigned flag) {
-#pragma unroll
-  for (int q = 0; q < K; ++q) wq[q * QSLOTS + r] = v[q];
-  wq[(K + 1) * QSLOTS + r] = __longlong_as_double(decided ? (0x100ll | flag) : 0ll);
-}
-
-/* the lanes in am work through queue items 0..n-1: FP64 decisions where undecided, then
-   the general reconstruction; item r's result goes to slot K, its flag byte to slot K + 1 */
-template <int K, int LIM>
-__device__ __forceinline__ void queue_process(double* wq, int n, unsigned am, const SchemeDev& S, int& st) {
-  const unsigned lt = (1u << (threadIdx.x & 31u)) - 1u;
-  const int wl = __popc(am & lt), na = __popc(am);
-  for (int base = 0; base < n; base += na) {
-    const int it = base + wl;
-    if (it < n) {
-      double v[K];
-#pragma unroll
-      for (int q = 0; q < K; ++q) v[q] = wq[q * QSLOTS + it];
-      const long long h = __double_as_longlong(wq[(K + 1) * QSLOTS + it]);
-      unsigned bits = (unsigned)h & 63u;
-      int ex = 7 + (int)((h >> 6) & 3);
-      if (!(h & 0x100ll)) teno_decide_fp64<K>(v, S, bits, ex, st);
-      wq[K * QSLOTS + it] = teno_general<K, LIM>(v, S, bits);
-      wq[(K + 1) * QSLOTS + it] = __longlong_as_double((long long)(bits | ((unsigned)((ex - 7) & 3) << 6)));
-    }
-  }
 }
 
 template <int K, int LIM, bool WT>
@@ -575,15 +505,9 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
   }
 }
 
-/* FUSE (x sweep only): tiles of FX_FACES faces overlap by one face, so that a tile holds
-   both faces of FX_FACES - 1 cells; after the faces, the tile differences them in shared
-   memory, adds the other axes' flux differences (their sweeps ran before) and applies the
-   stage combine, writing the stage output: the x faces never go to HBM and no separate
-   cell-update pass runs.  One x face in FX_FACES - 1 is computed twice. */
-template <int NV, int K, int LIM, int AXIS, bool REC = false, bool STATS = false, bool FUSE = false>
+template <int NV, int K, int LIM, int AXIS, bool REC = false, bool STATS = false>
 __global__ void __launch_bounds__(FaceTile<NV, K, AXIS>::THREADS, FACE_CTAS_PER_SM)
 face_kernel(const FaceArgs A) {
-  static_assert(!FUSE || (AXIS == 0 && !REC && !STATS), "the cell update is fused into the x sweep only");
   using T = FaceTile<NV, K, AXIS>;
   constexpr int H = T::H;
   extern __shared__ double sm[];
@@ -596,7 +520,7 @@ face_kernel(const FaceArgs A) {
     const int row = blockIdx.x;          /* y + ny * z */
     o1 = row % A.n[1];
     o2 = row / A.n[1];
-    f0 = blockIdx.y * (FUSE ? T::FACES - 1 : T::FACES);
+    f0 = blockIdx.y * T::FACES;
   } else {
     x0 = blockIdx.x * 32;
     f0 = blockIdx.y * T::FACES;
@@ -606,6 +530,8 @@ face_kernel(const FaceArgs A) {
   const long long sa = (AXIS == 0) ? sx : (AXIS == 1 ? sy : sz);
 
   /* --- phase 1: point quantities --- */
+  constexpr bool FWD = !REC && !STATS;
+  float* smf = reinterpret_cast<float*>(sm + (size_t)T::NCF * T::NP + T::FQDOUBLES);  /* forward kernels */
   int st = 0;
   for (int p = tid; p < T::NP; p += T::THREADS) {
     const int lane = (AXIS == 0) ? 0 : (p & 31);
@@ -622,7 +548,20 @@ face_kernel(const FaceArgs A) {
     double u[NV];
 #pragma unroll
     for (int q = 0; q < NV; ++q) u[q] = __ldg(A.U + q * A.ncell + cell);
-    if (A.P) {  /* primitives computed once per cell per stage (prim_kernel) */
+    if constexpr (FWD) {
+      double vel[NV - 2], pr, Hh, cs, sr;
+      if (A.P) {  /* primitives computed once per cell per stage (prim_kernel) */
+#pragma unroll
+        for (int d = 0; d < NV - 2; ++d) vel[d] = __ldg(A.P + d * A.ncell + cell);
+        pr = __ldg(A.P + (NV - 2) * A.ncell + cell);
+        Hh = __ldg(A.P + (NV - 1) * A.ncell + cell);
+        cs = __ldg(A.P + NV * A.ncell + cell);
+        sr = __ldg(A.P + (NV + 1) * A.ncell + cell);
+      } else {
+        point_prims<NV>(u, A.gamma, vel, pr, Hh, cs, sr, st);
+      }
+      stage_point_fwd<NV, AXIS>(u, vel, pr, Hh, cs, sr, sm, smf, T::NP, p);
+    } else if (A.P) {  /* primitives computed once per cell per stage (prim_kernel) */
       double vel[NV - 2];
 #pragma unroll
       for (int d = 0; d < NV - 2; ++d) vel[d] = __ldg(A.P + d * A.ncell + cell);
@@ -634,6 +573,10 @@ face_kernel(const FaceArgs A) {
     }
   }
   __syncthreads();
+  if constexpr (FWD) {  /* differences to the next point along the axis, for the screen */
+    for (int p = tid; p < T::NP - T::LANES; p += T::THREADS) stage_differences_fwd<NV, AXIS>(sm, smf, T::NP, p, p + T::LANES);
+    __syncthreads();
+  }
 
   /* --- phase 2: one face per thread --- */
   const int lane = (AXIS == 0) ? 0 : (tid & 31);
@@ -652,42 +595,19 @@ face_kernel(const FaceArgs A) {
     if (AXIS == 0) flin = f + (long long)(A.n[0] + 1) * (o1 + (long long)A.n[1] * o2);
     else if (AXIS == 1) flin = xg + (long long)A.n[0] * (f + (long long)(A.n[1] + 1) * o2);
     else flin = xg + (long long)A.n[0] * (o2 + (long long)A.n[1] * f);
-    face_flux_smem<NV, K, LIM, AXIS, T::LANES, REC, STATS>(
-        sm, T::NP, jf, lane, A.gamma, A.sch, Fh, A.flags ? A.flags + flin * NV * 2 : nullptr, st,
-        REC ? A.lin + flin : nullptr, A.nface, sm + T::NC * T::NP + (size_t)(tid >> 5) * QSLOTS * (K + 2), am,
-        cnt);
-    if constexpr (!STATS && !FUSE) {
+    if constexpr (FWD)
+      face_flux_fwd<NV, K, LIM, AXIS, T::LANES>(sm, smf, T::NP, jf, lane, A.gamma, A.sch, Fh,
+                                               A.flags ? A.flags + flin * NV * 2 : nullptr, st,
+                                               sm + (size_t)T::NCF * T::NP + (size_t)(tid >> 5) * FQCAP * fq_rows<NV>(),
+                                               am);
+    else
+      face_flux_smem<NV, K, LIM, AXIS, T::LANES, REC, STATS>(
+          sm, T::NP, jf, lane, A.gamma, A.sch, Fh, A.flags ? A.flags + flin * NV * 2 : nullptr, st,
+          REC ? A.lin + flin : nullptr, A.nface, sm + T::NC * T::NP + (size_t)(tid >> 5) * QSLOTS * (K + 2), am,
+          cnt);
+    if constexpr (!STATS) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) A.Fhat[v * A.nface + flin] = Fh[v];
-    }
-  }
-  if constexpr (FUSE) {
-    /* the tile's faces through shared memory (the point tile is no longer read), then one
-       thread per cell whose two x faces the tile holds */
-    __syncthreads();
-    if (active) {
-#pragma unroll
-      for (int v = 0; v < NV; ++v) sm[v * T::FACES + tid] = Fh[v];
-    }
-    __syncthreads();
-    const int cx = f0 + tid;
-    if (tid < T::FACES - 1 && cx < A.n[0]) {
-      const long long nc = A.ncell;
-      const long long yz = o1 + (long long)A.n[1] * o2;
-      const long long c = cx + (long long)A.n[0] * yz;
-      double dfx[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) dfx[v] = sm[v * T::FACES + tid + 1] - sm[v * T::FACES + tid];
-      long long fl[3] = {0, 0, 0}, fs[3] = {0, 0, 0};
-      if (NV > 3) {
-        fl[1] = cx + (long long)A.n[0] * (o1 + (long long)(A.n[1] + 1) * o2);
-        fs[1] = A.n[0];
-      }
-      if (NV > 4) {
-        fl[2] = c;
-        fs[2] = (long long)A.n[0] * A.n[1];
-      }
-      cell_update<NV>(A.cu, nc, c, dfx, fl, fs, A.cu.mode != 0 ? *A.cu.dt : 0.0);
     }
   }
   if constexpr (STATS) {  /* warp sums, one 64-bit atomic per counter and warp */

@@ -13,24 +13,17 @@ cudaError_t launch_face_nv5(const FaceArgs& a, int axis, int K, int lim, cudaStr
 cudaError_t launch_face_rec_nv3(const FaceArgs& a, int axis, int K, int lim, cudaStream_t st);
 cudaError_t launch_face_rec_nv4(const FaceArgs& a, int axis, int K, int lim, cudaStream_t st);
 cudaError_t launch_face_rec_nv5(const FaceArgs& a, int axis, int K, int lim, cudaStream_t st);
-/* The x sweep with the cell update fused (a.cu: the other axes' faces, states, stage). */
-cudaError_t launch_fused_nv3(const FaceArgs& a, int K, int lim, cudaStream_t st);
-cudaError_t launch_fused_nv4(const FaceArgs& a, int K, int lim, cudaStream_t st);
-cudaError_t launch_fused_nv5(const FaceArgs& a, int K, int lim, cudaStream_t st);
 /* The face kernel's decision statistics (tenom_stats.cuh) added to a.stats; no fluxes. */
 cudaError_t launch_stats_nv3(const FaceArgs& a, int axis, int K, int lim, cudaStream_t st);
 cudaError_t launch_stats_nv4(const FaceArgs& a, int axis, int K, int lim, cudaStream_t st);
 cudaError_t launch_stats_nv5(const FaceArgs& a, int axis, int K, int lim, cudaStream_t st);
 
-/* Launch geometry of a face sweep (kept in one place for the tests of the host logic).
-   fused: x tiles that overlap by one face (FX_FACES - 1 cells each, see face_kernel). */
-inline void face_grid(int nv, int axis, const int* n, int K, dim3* grid, dim3* block, bool fused = false) {
+/* Launch geometry of a face sweep (kept in one place for the tests of the host logic). */
+inline void face_grid(int nv, int axis, const int* n, int K, dim3* grid, dim3* block) {
   (void)nv;
   if (axis == 0) {
     *block = dim3(FX_FACES);
-    const int per = fused ? FX_FACES - 1 : FX_FACES;
-    const int units = fused ? n[0] : n[0] + 1;
-    *grid = dim3((unsigned)(n[1] * n[2]), (unsigned)((units + per - 1) / per));
+    *grid = dim3((unsigned)(n[1] * n[2]), (unsigned)((n[0] + 1 + FX_FACES - 1) / FX_FACES));
   } else {
     const int na = n[axis];
     const int other = (axis == 1) ? n[2] : n[1];

@@ -40,11 +40,11 @@ static cudaError_t ensure_smem_attr(Kern kern, AttrOnce& attr, size_t smem) {
 
 template <class Kern>
 static cudaError_t launch_tile(Kern kern, AttrOnce& attr, size_t smem, int nv, int axis, const int* n, int K,
-                               cudaStream_t st, const void* args_ptr, bool fused = false) {
+                               cudaStream_t st, const void* args_ptr) {
   cudaError_t e = ensure_smem_attr(kern, attr, smem);
   if (e != cudaSuccess) return e;
   dim3 grid, block;
-  face_grid(nv, axis, n, K, &grid, &block, fused);
+  face_grid(nv, axis, n, K, &grid, &block);
   void* argv[1] = {const_cast<void*>(args_ptr)};
   return cudaLaunchKernel((const void*)kern, grid, block, argv, smem, st);
 }
@@ -54,8 +54,8 @@ static cudaError_t launch_tile(Kern kern, AttrOnce& attr, size_t smem, int nv, i
 template <int NV, int K, int LIM, int AXIS, bool REC, bool STATS>
 static cudaError_t launch_face_one(const FaceArgs& a, cudaStream_t st) {
   static AttrOnce attr;
-  return launch_tile(face_kernel<NV, K, LIM, AXIS, REC, STATS>, attr, FaceTile<NV, K, AXIS>::SMEM_Q, NV, AXIS, a.n,
-                     K, st, &a);
+  return launch_tile(face_kernel<NV, K, LIM, AXIS, REC, STATS>, attr, face_smem<NV, K, AXIS, REC, STATS>(), NV, AXIS,
+                     a.n, K, st, &a);
 }
 
 template <int NV, int AXIS, bool REC, bool STATS>
@@ -82,28 +82,6 @@ static cudaError_t launch_face_nv(const FaceArgs& a, int axis, int K, int lim, c
     if (axis == 1) return launch_face_axis<NV, 1, REC, STATS>(a, K, lim, st);
   if constexpr (NV >= 5)
     if (axis == 2) return launch_face_axis<NV, 2, REC, STATS>(a, K, lim, st);
-  return cudaErrorNotSupported;
-}
-
-/* x sweep with the cell update fused */
-template <int NV, int K, int LIM>
-static cudaError_t launch_fused_one(const FaceArgs& a, cudaStream_t st) {
-  static AttrOnce attr;
-  return launch_tile(face_kernel<NV, K, LIM, 0, false, false, true>, attr, FaceTile<NV, K, 0>::SMEM_Q, NV, 0, a.n, K,
-                     st, &a, true);
-}
-
-template <int NV>
-static cudaError_t launch_fused_nv(const FaceArgs& a, int K, int lim, cudaStream_t st) {
-  if (K == 6) {
-    if (lim == LIM_MP) return launch_fused_one<NV, 6, LIM_MP>(a, st);
-    if (lim == LIM_TVD5) return launch_fused_one<NV, 6, LIM_TVD5>(a, st);
-    if (lim == LIM_VA) return launch_fused_one<NV, 6, LIM_VA>(a, st);
-  } else if (K == 8) {
-    if (lim == LIM_MP) return launch_fused_one<NV, 8, LIM_MP>(a, st);
-    if (lim == LIM_TVD5) return launch_fused_one<NV, 8, LIM_TVD5>(a, st);
-    if (lim == LIM_VA) return launch_fused_one<NV, 8, LIM_VA>(a, st);
-  }
   return cudaErrorNotSupported;
 }
 

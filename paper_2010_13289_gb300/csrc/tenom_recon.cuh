@@ -342,6 +342,140 @@ __device__ __forceinline__ bool cutoff_filter(const double (&D)[K - 1], const Sc
   return true;
 }
 
+/* Upper bound of sqrt(x) for x >= 0 from the fast reciprocal square root (within 2 ulp):
+   x rsqrt(x) is within 5u of sqrt(x); the factor 1 + 8u makes it an upper bound. */
+__device__ __forceinline__ float sqrt_up(float x) {
+  const float u = 5.9604645e-8f;
+  return x > 0.f ? x * rsqrtf(x) * (1.f + 8.f * u) : 0.f;
+}
+
+/* All-smooth screen of one split side from FP32 differences d[t] of the characteristic
+ * sequence, each known only to within an absolute error E (the projection done in FP32 on
+ * FP32 copies of the point data; the caller bounds E).  Returns true only when every
+ * candidate is certainly smooth (delta_k = 1 for every k, Eq. cut-off); otherwise the
+ * caller decides in FP64.  The decisions are bounded as in cutoff_filter (intervals of
+ * beta_k and tau carried through gamma_k and the comparison gamma_k >= C_T sum gamma),
+ * with these indicator bounds: the FP32 value of each beta = sum_j w_j t_j^2 on the given
+ * d is within C u beta_abs(|d|) <= C u k dmax^2 (k = beta_abs(1, .., 1), the form with
+ * |coefficients| on a vector of ones), and the error of d moves beta by at most
+ * 2 sqrt(beta(d) k) E + k E^2 (Cauchy-Schwarz on sum_j w_j 2 |t_j| sum_i |m_ji| E).
+ * TENO8A's [beta] (Eq. cut-off_adjust) is bounded by interval arithmetic: each eta_j over
+ * the box |Delta f| +- E (numerator and denominator bounded separately), the minimum,
+ * then m, g(m) and beta, which are monotone in eta; when both ends share one integer part
+ * the test uses that [beta]'s C_T, otherwise C_T = 1e-7, the largest 10^-[beta], which
+ * certifies the decisions for every [beta] (need_ex, for the flag byte: not certain). */
+template <int K>
+__device__ __forceinline__ bool screen_smooth(const float (&d)[K - 1], float E, const SchemeDev& S, bool need_ex,
+                                              int& ex) {
+  constexpr int c = K / 2 - 1;
+  constexpr int nk = K - 2;
+  const float u = 5.9604645e-8f;
+  const float C = 64.f * u;
+  float one[K - 1];
+  float dmax = 0.f;
+#pragma unroll
+  for (int t = 0; t < K - 1; ++t) {
+    one[t] = 1.f;
+    dmax = fmaxf(dmax, fabsf(d[t]));
+  }
+  if (!(dmax <= 1e15f) || !(E <= 1e14f)) return false;
+  const float dm2 = dmax * dmax;
+  float b[nk], kk[nk];
+  b[0] = beta0<c - 1, false, float>(d);
+  kk[0] = beta0<c - 1, true, float>(one);
+  b[1] = beta1<c, false, float>(d);
+  kk[1] = beta1<c, true, float>(one);
+  b[2] = beta2<c - 2, false, float>(d);
+  kk[2] = beta2<c - 2, true, float>(one);
+  b[3] = beta3<c, false, float>(d);
+  kk[3] = beta3<c, true, float>(one);
+  float bK, kK;
+  if constexpr (K == 8) {
+    b[4] = beta4<c - 3, false, float>(d);
+    kk[4] = beta4<c - 3, true, float>(one);
+    b[5] = beta5<c, false, float>(d);
+    kk[5] = beta5<c, true, float>(one);
+    bK = betaK8<0, false, float>(d);
+    kK = betaK8<0, true, float>(one);
+  } else {
+    bK = betaK6<0, false, float>(d);
+    kK = betaK6<0, true, float>(one);
+  }
+  auto err_of = [&](float bb, float kkb) {
+    const float r = kkb * (C * dm2);
+    return (r + kkb * E * E + 2.f * E * sqrt_up(kkb * (bb + r))) * (1.f + 16.f * u);
+  };
+  float er[nk];
+#pragma unroll
+  for (int k = 0; k < nk; ++k) er[k] = err_of(b[k], kk[k]);
+  const float comb = (b[1] + b[2] + 4.f * b[0]) * (1.f / 6.f);
+  const float dtau = (err_of(bK, kK) + (er[1] + er[2] + 4.f * er[0]) * (1.f / 6.f)) * (1.f + 8.f * u) +
+                     8.f * u * (bK + comb);
+  const float tau = fabsf(bK - comb);
+  const float tl = fmaxf(tau - dtau, 0.f), th = tau + dtau;
+  float xl[nk], xh[nk], xm = 1.f;
+#pragma unroll
+  for (int k = 0; k < nk; ++k) {
+    const float bl = b[k] - er[k], bh = (b[k] + er[k]) * (1.f + 2.f * u);
+    if (!(bl >= 1e-30f)) return false;  /* beta_k not bounded away from zero: undecided */
+    /* fast division within 2 ulp (4u): bl >= 1e-30, bh < 1e33 */
+    xl[k] = (1.f + __fdividef(tl, bh) * (1.f - 7.f * u)) * (1.f - u);
+    xh[k] = (1.f + __fdividef(th, bl) * (1.f + 7.f * u)) * (1.f + u);
+    if (!(xh[k] < 1e30f)) return false;
+    xm = fmaxf(xm, xh[k]);
+  }
+  const float rxm = __fdividef(1.f, xm);  /* a common scale of every gamma: its rounding cancels */
+  float gl[nk], Sh = 0.f;
+#pragma unroll
+  for (int k = 0; k < nk; ++k) {
+    const float yl = xl[k] * rxm * (1.f - 3.f * u), yh = xh[k] * rxm * (1.f + 3.f * u);
+    const float yl3 = yl * yl * yl, yh3 = yh * yh * yh;
+    gl[k] = yl3 * yl3 * (1.f - 8.f * u);
+    Sh += yh3 * yh3 * (1.f + 8.f * u);
+  }
+  Sh *= 1.f + 8.f * u;
+  float CTf = (S.ct_mode == CT_ADAPTIVE) ? 1e-7f : S.ct_const_f;
+  ex = 7;
+  if (S.ct_mode == CT_ADAPTIVE) {
+    const float xi = 1e-3f, Cr = 0.23f, a1 = 10.5f, a2 = 3.5f;
+    const float eps = 0.9f * Cr / (1.f - 0.9f * Cr) * xi * xi;
+    const float epl = eps * (1.f - 4.f * u), eph = eps * (1.f + 4.f * u);
+    float el = 1.f, eh = 1.f;  /* bounds of eta_{i+1/2}; eta <= 1 always */
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float ap = fabsf(d[c + q - 1]), am = fabsf(d[c + q - 2]);
+      const float apl = fmaxf(ap - E, 0.f), aml = fmaxf(am - E, 0.f), aph = ap + E, amh = am + E;
+      /* three roundings in each; 8u covers them and the rounding of the product itself */
+      const float nl = (2.f * apl * aml + epl) * (1.f - 8.f * u), nh = (2.f * aph * amh + eph) * (1.f + 8.f * u);
+      const float dl = (apl * apl + aml * aml + epl) * (1.f - 8.f * u),
+                  dh = (aph * aph + amh * amh + eph) * (1.f + 8.f * u);
+      el = fminf(el, __fdividef(nl, dh) * (1.f - 8.f * u));  /* fast division: 4u */
+      eh = fminf(eh, __fdividef(nh, dl) * (1.f + 8.f * u));
+    }
+    /* m decreases with eta, g decreases with m, beta increases with g */
+    const float rCr = 1.f / Cr;
+    const float mlo = 1.f - fminf(1.f, eh * rCr), mhi = 1.f - fminf(1.f, el * rCr);
+    const float olo = 1.f - mhi, ohi = 1.f - mlo;
+    const float glo = olo * olo * olo * olo * (1.f + 4.f * mhi), ghi = ohi * ohi * ohi * ohi * (1.f + 4.f * mlo);
+    const float blo = a1 - a2 * (1.f - glo) - 1e-5f, bhi = a1 - a2 * (1.f - ghi) + 1e-5f;
+    int xlo = (int)floorf(blo), xhi = (int)floorf(bhi);
+    xlo = xlo < 7 ? 7 : (xlo > 10 ? 10 : xlo);
+    xhi = xhi < 7 ? 7 : (xhi > 10 ? 10 : xhi);
+    if (xlo == xhi) {  /* [beta] certain: its C_T */
+      ex = xlo;
+      CTf = ex == 7 ? 1e-7f : (ex == 8 ? 1e-8f : (ex == 9 ? 1e-9f : 1e-10f));
+    } else if (need_ex) {
+      return false;    /* the flag byte needs [beta] */
+    }                  /* else C_T = 1e-7 bounds every [beta]'s C_T */
+  }
+  if (!(CTf >= 1e-30f)) return false;
+  const float thh = CTf * (1.f + 2.f * u) * Sh * (1.f + u);
+#pragma unroll
+  for (int k = 0; k < nk; ++k)
+    if (!(gl[k] >= thh)) return false;  /* not certainly chi_k >= C_T */
+  return true;
+}
+
 /* Candidate k's Table 1 coefficients on v (c = index of f_i), read off the generated
    candidate formulas applied to unit vectors (compile-time constants for a constant k). */
 template <int K>

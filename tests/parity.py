@@ -1,10 +1,13 @@
 """Parity rules between the CUDA path and the CPU oracle (test-side helper).
 
-Face values: |a - b| <= REL * max(|b|, S) where S is the magnitude of the terms of the
-characteristic back-projection sum_s r_s (f+_s + f-_s) that forms the face value (reported
-by the oracle): a face value that is small because those terms cancel is measured against
-the terms, as for any floating-point sum.  How many faces need S rather than |b| is
-counted and logged (strict_faces).
+Face values: |a - b| <= REL * max(|b|, S) where S is the magnitude of the terms summed to
+form the face value: the larger of the terms of the characteristic back-projection
+sum_s r_s (f+_s + f-_s) (reported by the oracle) and the terms of the K-point central
+flux sum_q |c_q| |F(U_q)| of the face's stencil (central_terms; where every field's
+candidates are smooth the face value is that central flux, whichever way it is summed).
+A face value that is small because those terms cancel is measured against the terms, as
+for any floating-point sum.  How many faces need S rather than |b| is counted and logged
+(strict_faces).
 Flags (delta_k bits and the adaptive C_T code): identical, except where the oracle's
 decision is ill-conditioned in FP64 -- its chi_k (or the adaptive beta) lies within
 CUT_TOL relative of the threshold, or within NOISE_K times the sequence's rounding-noise
@@ -157,3 +160,57 @@ def compare_cells(Ug, Uo, exclude=None, rel=1e-13, label=""):
                                  % (label, v, i, m, a[i], b[i]))
         worst = max(worst, m)
     return worst
+
+
+CENTRAL = {6: np.array([1, -8, 37, 37, -8, 1]) / 60.0,
+           8: np.array([-3, 29, -139, 533, 533, -139, 29, -3]) / 840.0}
+
+
+def central_terms(U, axis, K, bc, gamma=1.4):
+    """sum_q |c_q| |F_axis(U_{f-K/2+q})| per component and face of `axis` (x-first axis
+    index; U numpy [nv, (nz,) (ny,) nx]; bc 0 periodic, 1 zero-gradient): the magnitude of
+    the terms of the face's K-point central flux.  Returns [nv, face shape]."""
+    nv = U.shape[0]
+    nd = nv - 2
+    rho = U[0]
+    vel = [U[1 + d] / rho for d in range(nd)]
+    p = (gamma - 1.0) * (U[nv - 1] - 0.5 * sum(U[1 + d] * vel[d] for d in range(nd)))
+    un = vel[axis]
+    F = [U[0] * un] + [U[1 + d] * un + (p if d == axis else 0.0) for d in range(nd)] + [(U[nv - 1] + p) * un]
+    A = np.abs(np.stack(F))
+    ax = 1 + (nd - 1 - axis)  # numpy axis of the sweep axis in [nv, ...]
+    H = K // 2
+    pad = [(0, 0)] * A.ndim
+    pad[ax] = (H, H)
+    Ap = np.pad(A, pad, mode="wrap" if bc == 0 else "edge")
+    n = A.shape[ax]
+    out = 0.0
+    for q, cq in enumerate(CENTRAL[K]):
+        sl = [slice(None)] * A.ndim
+        sl[ax] = slice(q, q + n + 1)  # face f: cell f - H + q = padded index f + q
+        out = out + abs(cq) * Ap[tuple(sl)]
+    return out
+
+
+def central_terms_at(U, axis, K, bc, idx, gamma=1.4):
+    """central_terms at selected faces: idx[m, 3] = (x, y, z), the face index on `axis`.
+    Returns [nv, m]."""
+    nv = U.shape[0]
+    nd = nv - 2
+    n = U.shape[1:][::-1]  # (nx, ny, nz)
+    H = K // 2
+    out = np.zeros((nv, idx.shape[0]))
+    for q, cq in enumerate(CENTRAL[K]):
+        cell = idx[:, :nd].astype(np.int64).copy()
+        j = cell[:, axis] - H + q
+        j = np.mod(j, n[axis]) if bc == 0 else np.clip(j, 0, n[axis] - 1)
+        cell[:, axis] = j
+        sel = tuple(cell[:, d] for d in reversed(range(nd)))
+        u = np.stack([U[v][sel] for v in range(nv)])
+        rho = u[0]
+        vel = [u[1 + d] / rho for d in range(nd)]
+        p = (gamma - 1.0) * (u[nv - 1] - 0.5 * sum(u[1 + d] * vel[d] for d in range(nd)))
+        un = vel[axis]
+        F = [u[0] * un] + [u[1 + d] * un + (p if d == axis else 0.0) for d in range(nd)] + [(u[nv - 1] + p) * un]
+        out += abs(cq) * np.abs(np.stack(F))
+    return out

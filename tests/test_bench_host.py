@@ -28,10 +28,9 @@ def test_batch_config_counts_the_cells_and_flushes_l2():
 
 def test_launch_count_per_step():
     """Launches of one SSP-RK3 step: signal speed, dt and time update, then per stage the
-    primitives and one sweep per axis (the x sweep carries the cell update): 12 per step
-    in 2D, 15 in 3D; with the positivity limiter per stage also a limiter pass per axis
-    and a separate cell update: 21 in 2D (as the committed limited launch list counts:
-    126 solver launches over 6 steps)."""
-    assert bench.launches_per_step(2, False) == 3 + 3 * 3
-    assert bench.launches_per_step(3, False) == 3 + 3 * 4
+    primitives, one sweep per axis and the cell update: 15 per step in 2D, 18 in 3D; with
+    the positivity limiter per stage also a limiter pass per axis: 21 in 2D (the committed
+    limited launch list counts 126 solver launches over 6 steps)."""
+    assert bench.launches_per_step(2, False) == 3 + 3 * 4
+    assert bench.launches_per_step(3, False) == 3 + 3 * 5
     assert 6 * bench.launches_per_step(2, True) == 36 + 36 + 18 + 18 + 6 + 6 + 6

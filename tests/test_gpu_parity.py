@@ -6,7 +6,8 @@ import numpy as np
 import pytest
 
 from paper_2010_13289_gb300 import problems as PB
-from parity import CUT_TOL, NOISE_K, bound_counts, compare_cells, compare_faces, compare_rhs, dilate, switch_cells
+from parity import (CUT_TOL, NOISE_K, bound_counts, central_terms, central_terms_at, compare_cells, compare_faces,
+                    compare_rhs, dilate, switch_cells)
 
 pytestmark = pytest.mark.gpu
 
@@ -65,6 +66,7 @@ def test_face_flux_parity(T, orc, shape, bc, K, lim, jumps):
     for a in range(len(shape)):
         Fg, flg = S.face_dump(Ug, a)
         Fo, flo, cut, noise, bad, scale = orc.faces(g, so, Uo, a, with_scale=True)
+        scale = np.maximum(scale, central_terms(Uo, a, so.K, g.bc[a]))
         assert bad == 0
         st = compare_faces(Fg.cpu().numpy(), flg.cpu().numpy(), Fo, flo, cut, noise, scale,
                            label="%s axis %d" % (shape, a))
@@ -85,6 +87,7 @@ def face_parity_checks(T, orc, S, g, so, Uo, Ug, shape):
     for a in range(len(shape)):
         Fg, flg = S.face_dump(Ug, a)
         Fo, flo, cut, noise, bad, scale = orc.faces(g, so, Uo, a, with_scale=True)
+        scale = np.maximum(scale, central_terms(Uo, a, so.K, g.bc[a]))
         assert bad == 0
         st = compare_faces(Fg.cpu().numpy(), flg.cpu().numpy(), Fo, flo, cut, noise, scale,
                            label="%s axis %d" % (shape, a))
@@ -138,6 +141,7 @@ def step_switch_region(T, orc, S, g, so, Uo, dto, shape, K, label):
         for a in range(len(shape)):
             Fg, flg = S.face_dump(Xg, a)
             Fo, flo, cut, noise, bad, scale = orc.faces(g, so, X, a, with_scale=True)
+            scale = np.maximum(scale, central_terms(X, a, so.K, g.bc[a]))
             st = compare_faces(Fg.cpu().numpy(), flg.cpu().numpy(), Fo, flo, cut, noise, scale,
                                label="%s stage %d axis %d" % (label, st_i + 1, a))
             bound_counts(st)
@@ -241,6 +245,7 @@ def test_degenerate_sizes(T, orc, shape, bc, K):
     for a in range(len(shape)):
         Fg, flg = S.face_dump(Ug, a)
         Fo, flo, cut, noise, bad, scale = orc.faces(g, so, Uo, a, with_scale=True)
+        scale = np.maximum(scale, central_terms(Uo, a, so.K, g.bc[a]))
         st = compare_faces(Fg.cpu().numpy(), flg.cpu().numpy(), Fo, flo, cut, noise, scale,
                            label="degenerate %s axis %d" % (shape, a))
         bound_counts(st)
@@ -292,6 +297,7 @@ def check_sampled(T, orc, S, g, so, Ug, Uo, shape, m, seed, label="", smooth=Fal
         flg = flg.cpu().numpy()
         idx = sample_faces(rng, shape, a, m)
         Fo, flo, cut, noise, bad, scale = orc.faces_at(g, so, Uo, a, idx, with_scale=True)
+        scale = np.maximum(scale.T, central_terms_at(Uo, a, so.K, g.bc[a], idx)).T
         sel = tuple(idx[:, d] for d in reversed(range(len(shape))))
         Fgs = np.stack([Fg[v][sel] for v in range(len(shape) + 2)])
         st = compare_faces(Fgs, flg[sel], Fo.T, flo, cut, noise, scale.T, label="%s sampled axis %d" % (label, a))
@@ -369,6 +375,7 @@ def test_taylor_green_parity_and_conservation(T, orc):
     for a in range(3):
         Fg, flg = S.face_dump(Ug, a)
         Fo, flo, cut, noise, bad, scale = orc.faces(g, so, Uo, a, with_scale=True)
+        scale = np.maximum(scale, central_terms(Uo, a, so.K, g.bc[a]))
         assert bad == 0
         # the symmetric field makes face values vanish exactly on its symmetry planes, where
         # both sides return rounding noise of terms that cancel before the back-projection:
@@ -405,6 +412,7 @@ def test_decision_stats_match_oracle(T, orc, shape, bc, K, lim):
         cnt = S.decision_stats(Ug, a)
         c = T.stats_dict(cnt.cpu().numpy(), K)
         Fo, flo, cut, noise, bad, scale = orc.faces(g, so, Uo, a, with_scale=True)
+        scale = np.maximum(scale, central_terms(Uo, a, so.K, g.bc[a]))
         fl = flo.reshape(-1).astype(np.int64)
         cu, no = cut.reshape(-1), noise.reshape(-1)
         excused = int(((cu <= CUT_TOL) | (cu <= NOISE_K * no)).sum())

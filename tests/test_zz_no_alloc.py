@@ -31,6 +31,15 @@ def _p(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def close_per_component(got, want):
+    """Within 1e-13 of each component's largest value: the two calls form the cell
+    primitives in different kernels (in the tile here, once per cell in tenom_rhs), and a
+    cutoff decision set by rounding (a flat sequence at a zero-gradient boundary) may then
+    take the other branch, which moves the value at the level of the sequence's noise."""
+    for v in range(want.shape[0]):
+        np.testing.assert_allclose(got[v], want[v], rtol=0, atol=1e-13 * np.abs(want[v]).max())
+
+
 @pytest.mark.parametrize("shape,bc,K,lim", [((96, 80), (0, 1), 6, 0), ((40, 24, 16), (0, 0, 1), 8, 1),
                                             ((300,), (1,), 8, 0)])
 def test_noalloc_rhs_matches_tenom_rhs_twice(T, shape, bc, K, lim):
@@ -49,7 +58,7 @@ def test_noalloc_rhs_matches_tenom_rhs_twice(T, shape, bc, K, lim):
                                        stream)
         assert st == T.TENOM_OK
         torch.cuda.synchronize()
-        np.testing.assert_allclose(got.cpu().numpy(), want.cpu().numpy(), rtol=1e-13, atol=1e-13)
+        close_per_component(got.cpu().numpy(), want.cpu().numpy())
         assert status.item() == 0
     S.close()
 
@@ -81,7 +90,7 @@ def test_noalloc_status_word(T):
     st = T.lib().tenom_rhs_noalloc(ctypes.byref(grid), ctypes.byref(scheme), _p(U), _p(got), None, stream)
     assert st == T.TENOM_OK
     torch.cuda.synchronize()
-    np.testing.assert_allclose(got.cpu().numpy(), want.cpu().numpy(), rtol=1e-13, atol=1e-13)
+    close_per_component(got.cpu().numpy(), want.cpu().numpy())
 
     bad = U.clone()
     bad[3, 10, 20] = 0.5 * (bad[1, 10, 20] ** 2 + bad[2, 10, 20] ** 2) / bad[0, 10, 20] - 1.0  # p < 0
