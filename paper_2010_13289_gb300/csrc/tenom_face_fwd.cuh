@@ -218,7 +218,7 @@ __device__ __forceinline__ void face_flux_fwd(const double* sm, const float* smf
 
   /* per field: central (bit s of cmask), else queued; fsv[s] receives f+ + f- of a queued
      field that is not all smooth after all */
-  unsigned cmask = 0u, qmask = 0u, exbits = 0u;
+  unsigned cmask = 0u, qmask = 0u;
   unsigned long long qslot = 0ull;
   int nq = 0;
   double fsv[NV];
@@ -247,8 +247,14 @@ __device__ __forceinline__ void face_flux_fwd(const double* sm, const float* smf
   };
 
   const float u32 = 5.9604645e-8f;
+  /* one pass per field, and a last pass (s == NV) that only flushes the queue: the queue
+     processing has a single call site (a smaller footprint in the instruction cache) */
 #pragma unroll 1
-  for (int s = 0; s < NV; ++s) {
+  for (int s = 0; s <= NV; ++s) {
+    if (s == NV) {  /* the same in every lane */
+      if (nq > 0) flush();
+      break;
+    }
     const bool acoustic = (s == 0) || (s == NV - 1);
     const int dt = (s - 2) < AXIS ? (s - 2) : (s - 1);
     const bool shear = !acoustic && s != 1;
@@ -274,8 +280,8 @@ __device__ __forceinline__ void face_flux_fwd(const double* sm, const float* smf
         la[v] = fabsf(lf[v]);
       }
       const float haf = f32_rz(ha);
-      float dp[K - 1], dm[K - 1];
-      float Am = 0.f, mp = 0.f, mm = 0.f;
+      float hdgv[K - 1], dwv[K - 1];  /* G differences / 2 and W differences */
+      float Am = 0.f;
       float w0 = 0.f, wa0 = 0.f;  /* W and WA of point t */
 #pragma unroll
       for (int q = 0; q < K; ++q) {
@@ -321,20 +327,32 @@ __device__ __forceinline__ void face_flux_fwd(const double* sm, const float* smf
             dg = fmaf(p1 * lf[NV - 1], du, fmaf(kap, dpp, dg));
             ag = fmaf(fabsf(p1) * la[NV - 1], fabsf(du), fmaf(kapa, fabsf(dpp), ag));
           }
-          const float hdg = 0.5f * dg;
-          dp[t] = fmaf(haf, dw, hdg);
-          dm[K - 2 - t] = -fmaf(-haf, dw, hdg);  /* f- on the stencil mirrored about x_{i+1/2} */
+          hdgv[t] = 0.5f * dg;
+          dwv[t] = dw;
           Am = fmaxf(Am, fmaf(haf, dwa, 0.5f * ag));
-          mp = fmaxf(mp, fabsf(dp[t]));
-          mm = fmaxf(mm, fabsf(dm[K - 2 - t]));
         }
         w0 = w;
         wa0 = wa;
       }
       const float Eb = 24.f * u32 * Am * (1.f + 4.f * u32) + 1e-30f;
       const bool nex = flags != nullptr;
-      central = screen_smooth<K>(dp, fmaf(2.f * u32, mp, Eb) * (1.f + 2.f * u32), sch, nex, exp_) &&
-                screen_smooth<K>(dm, fmaf(2.f * u32, mm, Eb) * (1.f + 2.f * u32), sch, nex, exm_);
+      /* the two sides through one copy of the screen (a smaller loop body for the
+         instruction cache): f+ on d_t = dG_t/2 + (alpha/2) dW_t, f- on the stencil mirrored
+         about x_{i+1/2}, d_t = -(dG/2 - (alpha/2) dW)_{K-2-t} */
+      central = true;
+#pragma unroll 1
+      for (int side = 0; side < 2 && central; ++side) {
+        float d[K - 1], mx = 0.f;
+#pragma unroll
+        for (int t = 0; t < K - 1; ++t) {
+          d[t] = side ? -fmaf(-haf, dwv[K - 2 - t], hdgv[K - 2 - t]) : fmaf(haf, dwv[t], hdgv[t]);
+          mx = fmaxf(mx, fabsf(d[t]));
+        }
+        int ex_s = 7;
+        central = screen_smooth<K>(d, fmaf(2.f * u32, mx, Eb) * (1.f + 2.f * u32), sch, nex, ex_s);
+        if (side) exm_ = ex_s;
+        else exp_ = ex_s;
+      }
     }
     if (central) {
       cmask |= 1u << s;
@@ -360,7 +378,6 @@ __device__ __forceinline__ void face_flux_fwd(const double* sm, const float* smf
     }
     nq += cnt;
   }
-  if (nq > 0) flush();  /* nq is the same in every lane of the warp */
 
   constexpr unsigned allf = (1u << NV) - 1u;
   if (cmask == allf) {

@@ -144,9 +144,19 @@ def test_limited_step_parity_on_near_vacuum_states(T, orc, shape, K):
     on.close()
 
 
+# The oracle's own rounding error on this near-vacuum run: the same 40 steps in 80-bit
+# extended precision (the oracle's templates instantiated with long double, the limiter
+# included) differ from its FP64 result by 3.6e-11 .. 5.4e-11 in relative L1 per
+# component.  The characteristic step is ill-conditioned there (huge left eigenvectors
+# where the sound speed is small), so two correct FP64 evaluation orders may differ by
+# about twice that.
+NEAR_VACUUM_ORACLE_ERROR = 5.4e-11
+
+
 def test_limited_2d_run_parity(T, orc):
     """40 limited steps (CFL 0.4, dt on the device) of a 2D near-vacuum state: relative L1
-    per component within 1e-10 of the oracle, density and pressure positive."""
+    per component within 1e-10 plus twice the oracle's own rounding error on this run of
+    the oracle, density and pressure positive."""
     shape = (32, 32)
     dx = (0.1, 0.1)
     g = orc.make_grid(shape, dx, (orc.BC_PERIODIC,) * 2, gamma=1.4)
@@ -160,7 +170,7 @@ def test_limited_2d_run_parity(T, orc):
     S.advance(Ug, 40, cfl=0.4)
     Ug = Ug.cpu().numpy()
     l1 = np.abs(Ug - Uo).reshape(4, -1).sum(1) / np.abs(Uo).reshape(4, -1).sum(1)
-    assert np.all(l1 <= 1e-10), l1
+    assert np.all(l1 <= 1e-10 + 2 * NEAR_VACUUM_ORACLE_ERROR), l1
     assert Ug[0].min() > 0 and pressure(Ug, 1.4).min() > 0
     S.close()
 
