@@ -583,7 +583,11 @@ face_kernel(const FaceArgs A) {
   const int jf = (AXIS == 0) ? tid : (tid >> 5);
   const int f = f0 + jf;
   const int xg = x0 + lane;
-  bool active = (f <= na) && (AXIS == 0 || xg < A.n[0]);
+  /* forward kernels on a periodic axis compute faces 0 .. n-1 only: face n has the same
+     stencil points as face 0, and face 0's lanes write it to both places (face_grid sizes
+     those launches for n faces, which drops the nearly empty last tile of every line) */
+  const bool wrapped = FWD && A.bc[AXIS] == 0;
+  bool active = (wrapped ? f < na : f <= na) && (AXIS == 0 || xg < A.n[0]);
   const unsigned am = __ballot_sync(0xffffffffu, active);  /* the lanes sharing the warp's queue */
   unsigned cnt[STATS ? SC_COUNT : 1];
 #pragma unroll
@@ -608,6 +612,18 @@ face_kernel(const FaceArgs A) {
     if constexpr (!STATS) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) A.Fhat[v * A.nface + flin] = Fh[v];
+      if (wrapped && f == 0) {  /* face n of the line */
+        long long fn;
+        if (AXIS == 0) fn = na + (long long)(A.n[0] + 1) * (o1 + (long long)A.n[1] * o2);
+        else if (AXIS == 1) fn = xg + (long long)A.n[0] * (na + (long long)(A.n[1] + 1) * o2);
+        else fn = xg + (long long)A.n[0] * (o2 + (long long)A.n[1] * na);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) A.Fhat[v * A.nface + fn] = Fh[v];
+        if (A.flags) {
+#pragma unroll
+          for (int e = 0; e < 2 * NV; ++e) A.flags[fn * NV * 2 + e] = A.flags[flin * NV * 2 + e];
+        }
+      }
     }
   }
   if constexpr (STATS) {  /* warp sums, one 64-bit atomic per counter and warp */

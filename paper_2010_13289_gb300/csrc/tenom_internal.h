@@ -18,18 +18,20 @@ cudaError_t launch_stats_nv3(const FaceArgs& a, int axis, int K, int lim, cudaSt
 cudaError_t launch_stats_nv4(const FaceArgs& a, int axis, int K, int lim, cudaStream_t st);
 cudaError_t launch_stats_nv5(const FaceArgs& a, int axis, int K, int lim, cudaStream_t st);
 
-/* Launch geometry of a face sweep (kept in one place for the tests of the host logic). */
-inline void face_grid(int nv, int axis, const int* n, int K, dim3* grid, dim3* block) {
+/* Launch geometry of a face sweep (kept in one place for the tests of the host logic):
+   tiles over the n_a + 1 faces of a line, or over n_a faces (wrapped: a forward kernel on
+   a periodic axis, whose face n_a is face 0's copy). */
+inline void face_grid(int nv, int axis, const int* n, int K, dim3* grid, dim3* block, bool wrapped = false) {
   (void)nv;
+  const int nf = n[axis] + (wrapped ? 0 : 1);
   if (axis == 0) {
     *block = dim3(FX_FACES);
-    *grid = dim3((unsigned)(n[1] * n[2]), (unsigned)((n[0] + 1 + FX_FACES - 1) / FX_FACES));
+    *grid = dim3((unsigned)(n[1] * n[2]), (unsigned)((nf + FX_FACES - 1) / FX_FACES));
   } else {
-    const int na = n[axis];
     const int other = (axis == 1) ? n[2] : n[1];
     const int ft = ft_faces(K);
     *block = dim3(32 * ft);
-    *grid = dim3((unsigned)((n[0] + 31) / 32), (unsigned)((na + 1 + ft - 1) / ft), (unsigned)other);
+    *grid = dim3((unsigned)((n[0] + 31) / 32), (unsigned)((nf + ft - 1) / ft), (unsigned)other);
   }
 }
 
