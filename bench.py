@@ -53,8 +53,8 @@ FP64_NOMINAL = 1.25e12  # FLOP/s, GB300 FP64 (an FMA counts 2)
 FP64_LANES_PER_CLK = 304  # FP64 pipe: 2 lanes per clock per SM x 152 SMs
 
 
-FACE_SOURCES = ("tenom_face.cuh", "tenom_recon.cuh", "tenom_linear.cuh", "teno_coeffs.cuh", "tenom_fastmath.cuh",
-                "tenom_launch.cuh")
+FACE_SOURCES = ("tenom_face.cuh", "tenom_face_fwd.cuh", "tenom_queue.cuh", "tenom_recon.cuh", "tenom_linear.cuh",
+                "tenom_stats.cuh", "teno_coeffs.cuh", "tenom_fastmath.cuh", "tenom_launch.cuh", "tenom_internal.h")
 
 
 def face_source_hash():
@@ -545,6 +545,14 @@ def face_roofline(name, shape, nv, face_ms, face_launches, clk, probe_flops):
                     if face_ms > 0 and hbm_peak else None}}
     if fig:
         roof["fp64_pipe_busy_ncu"] = float(fig["fp64_pipe_busy"])
+        if "warp_inst_per_face" in fig and face_ms > 0:
+            # the SM schedulers' issue slots: 4 warp instructions per clock per SM
+            wi = float(fig["warp_inst_per_face"]) * faces_per_launch / (face_ms * 1e-3)
+            ipeak = 4 * 152 * smax * 1e6
+            roof["issue"] = {"warp_inst_per_face": float(fig["warp_inst_per_face"]), "achieved": wi,
+                             "peak": ipeak, "unit": "warp inst/s", "frac": wi / ipeak,
+                             "note": "all instructions issued (FP32 screen, integer, loads, FP64) against "
+                                     "4 per clock per SM x 152 SMs at the maximum SM clock"}
     fpf = flops_per_face(name)
     if fpf and face_ms > 0:
         roof["oracle_equivalent_rate"] = {
@@ -1022,7 +1030,9 @@ def measure_adjoint(name, tape="auto", rollout_steps=0, fd_dirs=16, fd_steps=(1e
             fd["%g" % h] = {"max_err_over_grad_norm": max(errs) if errs else None,
                             "median_err_over_grad_norm": float(np.median(errs)) if errs else None,
                             "median_err_over_directional_derivative": float(np.median(rel)) if rel else None}
-    best = min(fd, key=lambda k: fd[k]["max_err_over_grad_norm"]) if fd else None
+    best = min(fd, key=lambda k: fd[k]["max_err_over_grad_norm"]) if fd_dirs > 0 and fd else None
+    if fd_dirs == 0:
+        fd = {}
     S.close()
     return {"workload": name, "shape": [n, n], "K": K, "limiter": "MP" if lim == 0 else "TVD5", "steps": steps,
             "window": win_n, "checkpoint_every": every, "dt": dt, "tape": tape,
