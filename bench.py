@@ -49,7 +49,6 @@ ADJOINT_WORKLOADS = {
 }
 DEFAULT = "solenoidal_3d_256_teno8_mp"
 ADJOINT_DEFAULT = "adjoint_broadband_2d_512_teno6_mp"
-FP64_NOMINAL = 1.25e12  # FLOP/s, GB300 FP64 (an FMA counts 2)
 FP64_LANES_PER_CLK = 304  # FP64 pipe: 2 lanes per clock per SM x 152 SMs
 
 
@@ -57,20 +56,24 @@ FACE_SOURCES = ("tenom_face.cuh", "tenom_face_fwd.cuh", "tenom_queue.cuh", "teno
                 "tenom_stats.cuh", "teno_coeffs.cuh", "tenom_fastmath.cuh", "tenom_launch.cuh", "tenom_internal.h")
 
 
-def face_source_hash():
-    """Hash of the sources the face kernel is compiled from (tags the ncu figures)."""
+BATCH_SOURCES = FACE_SOURCES + ("tenom_batch.cu", "tenom_batch_kernel.cuh", "tenom_positivity.cuh")
+
+
+def face_source_hash(sources=FACE_SOURCES):
+    """Hash of the sources a kernel is compiled from (tags the ncu figures)."""
     import hashlib
     h = hashlib.sha256()
-    for f in FACE_SOURCES:
+    for f in sources:
         with open(os.path.join(ROOT, "paper_2010_13289_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profile_figures(name):
-    """ncu figures of the face kernel committed for this workload (profiles/), or None when
-    there are none or they were taken from other kernel sources than the ones built now."""
-    path = os.path.join(ROOT, "profiles", "face_kernel_%s.md" % name)
+def profile_figures(name, kernel="face_kernel", sources=FACE_SOURCES):
+    """ncu figures of a kernel committed for this workload (profiles/<kernel>_<name>.md), or
+    None when there are none or they were taken from other kernel sources than the ones
+    built now."""
+    path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, name))
     if not os.path.exists(path):
         return None
     fig, inside = {}, False
@@ -82,7 +85,7 @@ def profile_figures(name):
         elif inside and ":" in line:
             k, v = line.split(":", 1)
             fig[k.strip()] = v.strip()
-    if fig.get("source_sha256") != face_source_hash():
+    if fig.get("source_sha256") != face_source_hash(sources):
         return None
     fig["file"] = os.path.relpath(path, ROOT)
     return fig
@@ -563,6 +566,36 @@ def face_roofline(name, shape, nv, face_ms, face_launches, clk, probe_flops):
     return roof
 
 
+def batch_roofline(name, faces, stage_ms, probe_flops):
+    """Roofline of the batched stage kernel (faces, flux difference and stage combine of
+    every problem in one persistent launch), on the same unit as the face kernel's: FP64
+    thread instructions per face (ncu, committed under profiles/ for these kernel sources)
+    x faces per launch / the CUDA-event launch time, against the DFMA probe's measured
+    instruction rate."""
+    probe_inst = probe_flops / 2.0
+    fig = profile_figures(name, kernel="batch_stage_kernel", sources=BATCH_SOURCES)
+    ipf = float(fig["fp64_thread_instr_per_face"]) if fig else None
+    achieved = ipf * faces / (stage_ms * 1e-3) if ipf and stage_ms > 0 else None
+    roof = {"bound": "alu", "achieved": achieved, "peak": probe_inst, "unit": "FP64 inst/s",
+            "frac": achieved / probe_inst if achieved else None,
+            "traffic": float(fig["dram_bytes_per_launch"]) if fig else None,
+            "kernel": "batch_stage_kernel (persistent faces + flux difference + stage combine)",
+            "fp64_inst_per_face": ipf, "faces_per_launch": faces, "ms_per_launch": stage_ms,
+            "peak_note": "measured: DFMA probe (8 independent FMA chains per thread) in FP64 instructions/s",
+            "achieved_note": ("ncu FP64 thread instructions per face from %s (same kernel sources) x faces per "
+                              "launch / CUDA-event launch time" % fig["file"]) if fig else
+                             "no ncu count for these kernel sources: achieved and traffic unmeasured"}
+    if fig:
+        roof["fp64_pipe_busy_ncu"] = float(fig["fp64_pipe_busy"])
+    fpf = flops_per_face(name)
+    if fpf and stage_ms > 0:
+        roof["oracle_equivalent_rate"] = {
+            "flops_per_face": fpf, "flop_per_s": fpf * faces / (stage_ms * 1e-3),
+            "note": "the oracle's op count of the textbook formulation per face over the launch time; not "
+                    "bounded by the FP64 peak"}
+    return roof
+
+
 def measured_hbm_gbs():
     """HBM copy bandwidth of this machine's GPUs (GB/s) from the generated peaks file."""
     try:
@@ -680,14 +713,8 @@ def run_batch(args):
     e2e = float(B.total) * 3 * e2e_steps * ws / e2e_s
     state_bytes = 8 * 3 * B.total
 
-    fpf = flops_per_face(name)
     faces = float(np.sum(sizes + 1))
-    achieved = fpf * faces / (stage_ms * 1e-3)
-    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL, "unit": "FLOP/s",
-            "frac": achieved / FP64_NOMINAL, "traffic": None,
-            "kernel": "batch_stage_kernel (persistent faces + flux difference + stage combine)",
-            "flops_per_face": fpf, "faces_per_launch": faces, "ms_per_launch": stage_ms,
-            "peak_note": "nominal GB300 FP64 (FMA = 2 flops)"}
+    roof = batch_roofline(name, faces, stage_ms, T.fp64_peak())
     out = {"metric": "cell-updates/s per RK stage (FP64)", "value": value, "unit": "cell-updates/s",
            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
