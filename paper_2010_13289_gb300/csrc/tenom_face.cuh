@@ -75,8 +75,8 @@ struct FaceTile {
      the FP32 copies of the point data */
   static constexpr int NCF = PointLayoutF<NV>::NC;
   static constexpr size_t FQDOUBLES = (size_t)(THREADS / 32) * FQCAP * fq_rows<NV>();
-  static constexpr size_t SMEM_FWD =
-      sizeof(double) * ((size_t)NCF * NP + FQDOUBLES) + sizeof(float) * (size_t)PointLayoutF<NV>::NF * NP;
+  static constexpr size_t SMEM_FWD = sizeof(double) * ((size_t)NCF * NP + FQDOUBLES) +
+                                     sizeof(float) * (size_t)PointLayoutF<NV>::NF * NP + sizeof(int) * (THREADS / 32);
 };
 
 /* dynamic shared memory of face_kernel<..., REC, STATS, ...> */
@@ -573,6 +573,7 @@ face_kernel(const FaceArgs A) {
     }
   }
   __syncthreads();
+  int* wq_n = reinterpret_cast<int*>(smf + (size_t)PointLayoutF<NV>::NF * T::NP);  /* forward: queue lengths */
   if constexpr (FWD) {  /* differences to the next point along the axis, for the screen */
     for (int p = tid; p < T::NP - T::LANES; p += T::THREADS) stage_differences_fwd<NV, AXIS>(sm, smf, T::NP, p, p + T::LANES);
     __syncthreads();
@@ -593,22 +594,44 @@ face_kernel(const FaceArgs A) {
 #pragma unroll
   for (int q = 0; q < (STATS ? SC_COUNT : 1); ++q) cnt[q] = 0u;
   double Fh[NV];
+  /* face linear index (n_a + 1 entries along the axis) */
+  long long flin = 0;
+  if (AXIS == 0) flin = f + (long long)(A.n[0] + 1) * (o1 + (long long)A.n[1] * o2);
+  else if (AXIS == 1) flin = xg + (long long)A.n[0] * (f + (long long)(A.n[1] + 1) * o2);
+  else flin = xg + (long long)A.n[0] * (o2 + (long long)A.n[1] * f);
+  uint8_t* const flg = (active && A.flags) ? A.flags + flin * NV * 2 : nullptr;
+  if constexpr (FWD) {
+    /* screen every field, queue the rest; the CTA works through the queues together (more
+       than one round only when a warp's queue fills) */
+    constexpr int W = T::THREADS / 32;
+    double* const fq0 = sm + (size_t)T::NCF * T::NP;
+    double* const fq = fq0 + (size_t)(tid >> 5) * FQCAP * fq_rows<NV>();
+    FwdFace<NV, K, LIM, AXIS, T::LANES> F;
+    if (active) F.begin(sm, T::NP, jf, lane, A.gamma, st);
+    const int rot = (int)((blockIdx.x + blockIdx.y + blockIdx.z) % W);
+    bool again = true;
+#pragma unroll 1
+    while (again) {
+      bool stopped = false;
+      int mine = 0;
+      if (active && F.s_next < NV) {
+        stopped = !F.fields(smf, T::NP, jf, lane, A.sch, flg, fq, am);
+        mine = F.nq;
+      }
+      const int wn = __reduce_max_sync(0xffffffffu, mine);
+      if ((tid & 31) == 0) wq_n[tid >> 5] = wn;
+      __syncthreads();
+      field_queue_cta<NV, K, LIM, AXIS, T::LANES, T::THREADS>(sm, T::NP, fq0, wq_n, A.sch, st, rot);
+      again = __syncthreads_or(stopped);
+      if (active) F.readback(fq, flg, A.sch);
+    }
+    if (active) F.finish(Fh);
+  }
   if (active) {
-    /* face linear index (n_a + 1 entries along the axis) */
-    long long flin;
-    if (AXIS == 0) flin = f + (long long)(A.n[0] + 1) * (o1 + (long long)A.n[1] * o2);
-    else if (AXIS == 1) flin = xg + (long long)A.n[0] * (f + (long long)(A.n[1] + 1) * o2);
-    else flin = xg + (long long)A.n[0] * (o2 + (long long)A.n[1] * f);
-    if constexpr (FWD)
-      face_flux_fwd<NV, K, LIM, AXIS, T::LANES>(sm, smf, T::NP, jf, lane, A.gamma, A.sch, Fh,
-                                               A.flags ? A.flags + flin * NV * 2 : nullptr, st,
-                                               sm + (size_t)T::NCF * T::NP + (size_t)(tid >> 5) * FQCAP * fq_rows<NV>(),
-                                               am);
-    else
+    if constexpr (!FWD)
       face_flux_smem<NV, K, LIM, AXIS, T::LANES, REC, STATS>(
-          sm, T::NP, jf, lane, A.gamma, A.sch, Fh, A.flags ? A.flags + flin * NV * 2 : nullptr, st,
-          REC ? A.lin + flin : nullptr, A.nface, sm + T::NC * T::NP + (size_t)(tid >> 5) * QSLOTS * (K + 2), am,
-          cnt);
+          sm, T::NP, jf, lane, A.gamma, A.sch, Fh, flg, st, REC ? A.lin + flin : nullptr, A.nface,
+          sm + T::NC * T::NP + (size_t)(tid >> 5) * QSLOTS * (K + 2), am, cnt);
     if constexpr (!STATS) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) A.Fhat[v * A.nface + flin] = Fh[v];

@@ -16,9 +16,9 @@
  * g+-_q = (G_q +- alpha W_q)/2 are projected in FP32 from FP32 copies of the point data,
  * with a rigorous bound E on each difference, and screen_smooth certifies that every
  * candidate is smooth over that error box.  The other fields are queued per warp (their
- * l_s and alpha/2) and the warp's active lanes then work through the queue together:
+ * l_s and alpha/2) and the CTA's threads then work through all its warps' queues together:
  * FP64 projection from the tile, certified or FP64 decisions, central formula or
- * general reconstruction, so the FP64 work runs with full lanes.  A queued field whose
+ * general reconstruction, so the FP64 work runs in as few, as full warps as it can.  A queued field whose
  * two sides turn out all smooth is central too (fs = l_s . Fc), so the result does not
  * depend on which test decided.  The physical flux is not staged:
  * G = l . F(U) = u_n (l . U) + p (l_{1+a} + u_n l_E).
@@ -70,57 +70,75 @@ constexpr int FQCAP = 64;
 template <int NV>
 __host__ __device__ constexpr int fq_rows() { return NV + 3; }
 
-/* the warp's lanes in am work through field items 0..n-1 */
+/* one queued field: FP64 projection of its K points, decisions of both split sides
+   (certified FP32 filter, else FP64), reconstruction; result and flags into its slot */
 template <int NV, int K, int LIM, int AXIS, int LANES>
-__device__ __forceinline__ void field_queue_process(const double* sm, int NP, double* fq, int n, unsigned am,
-                                                    const SchemeDev& S, int& st) {
+__device__ __forceinline__ void field_queue_item(const double* sm, int NP, double* fq, int it, const SchemeDev& S,
+                                                 int& st) {
   using L = PointLayoutF<NV>;
   constexpr unsigned all = (1u << (K - 2)) - 1u;
-  const unsigned lt = (1u << (threadIdx.x & 31u)) - 1u;
-  const int wl = __popc(am & lt), na = __popc(am);
-  for (int base = 0; base < n; base += na) {
-    const int it = base + wl;
-    if (it < n) {
-      const long long h = __double_as_longlong(fq[(NV + 1) * FQCAP + it]);
-      const int jf = (int)(h & 0xffff), ln = (int)((h >> 16) & 31), s = (int)((h >> 21) & 7);
-      double l[NV];
+  const long long h = __double_as_longlong(fq[(NV + 1) * FQCAP + it]);
+  const int jf = (int)(h & 0xffff), ln = (int)((h >> 16) & 31), s = (int)((h >> 21) & 7);
+  double l[NV];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) l[v] = fq[v * FQCAP + it];
-      const double ha = fq[NV * FQCAP + it];
-      const int dt = (s - 2) < AXIS ? (s - 2) : (s - 1);
-      const bool shear = s >= 2 && s <= NV - 2;
-      auto P = [&](int comp, int q) -> double { return sm[comp * NP + (jf + q) * LANES + ln]; };
-      double gp[K], gm[K];
+  for (int v = 0; v < NV; ++v) l[v] = fq[v * FQCAP + it];
+  const double ha = fq[NV * FQCAP + it];
+  const int dt = (s - 2) < AXIS ? (s - 2) : (s - 1);
+  const bool shear = s >= 2 && s <= NV - 2;
+  auto P = [&](int comp, int q) -> double { return sm[comp * NP + (jf + q) * LANES + ln]; };
+  double gp[K], gm[K];
 #pragma unroll
-      for (int q = 0; q < K; ++q) {
-        const double un = P(L::cV + AXIS, q), pq = P(L::cP, q);
-        double w, kap;
-        if (shear) {
-          w = fma(l[0], P(L::cU, q), P(L::cU + 1 + dt, q));
-          kap = 0.0;
-        } else {
-          w = l[0] * P(L::cU, q);
+  for (int q = 0; q < K; ++q) {
+    const double un = P(L::cV + AXIS, q), pq = P(L::cP, q);
+    double w, kap;
+    if (shear) {
+      w = fma(l[0], P(L::cU, q), P(L::cU + 1 + dt, q));
+      kap = 0.0;
+    } else {
+      w = l[0] * P(L::cU, q);
 #pragma unroll
-          for (int v = 1; v < NV; ++v) w = fma(l[v], P(L::cU + v, q), w);
-          kap = fma(un, l[NV - 1], l[1 + AXIS]);
-        }
-        const double hg = 0.5 * fma(pq, kap, un * w);  /* G/2 = (u_a W + p kappa)/2 */
-        gp[q] = fma(ha, w, hg);
-        gm[q] = fma(-ha, w, hg);
-      }
-      double vm[K];
-#pragma unroll
-      for (int q = 0; q < K; ++q) vm[q] = gm[K - 1 - q];  /* f- on the stencil mirrored about x_{i+1/2} */
-      unsigned bp = 0, bm = 0;
-      int ep = 7, em = 7;
-      if (!teno_decide_fast<K>(gp, S, bp, ep)) teno_decide_fp64<K>(gp, S, bp, ep, st);
-      if (!teno_decide_fast<K>(vm, S, bm, em)) teno_decide_fp64<K>(vm, S, bm, em, st);
-      const double f = teno_general<K, LIM>(gp, S, bp) + teno_general<K, LIM>(vm, S, bm);
-      const unsigned flp = bp | ((unsigned)((ep - 7) & 3) << 6), flm = bm | ((unsigned)((em - 7) & 3) << 6);
-      const unsigned sm2 = (bp == all ? 1u : 0u) | (bm == all ? 2u : 0u);
-      fq[(NV + 2) * FQCAP + it] = f;
-      fq[(NV + 1) * FQCAP + it] = __longlong_as_double((long long)(flp | (flm << 8) | (sm2 << 16)));
+      for (int v = 1; v < NV; ++v) w = fma(l[v], P(L::cU + v, q), w);
+      kap = fma(un, l[NV - 1], l[1 + AXIS]);
     }
+    const double hg = 0.5 * fma(pq, kap, un * w);  /* G/2 = (u_a W + p kappa)/2 */
+    gp[q] = fma(ha, w, hg);
+    gm[q] = fma(-ha, w, hg);
+  }
+  double vm[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) vm[q] = gm[K - 1 - q];  /* f- on the stencil mirrored about x_{i+1/2} */
+  unsigned bp = 0, bm = 0;
+  int ep = 7, em = 7;
+  if (!teno_decide_fast<K>(gp, S, bp, ep)) teno_decide_fp64<K>(gp, S, bp, ep, st);
+  if (!teno_decide_fast<K>(vm, S, bm, em)) teno_decide_fp64<K>(vm, S, bm, em, st);
+  const double f = teno_general<K, LIM>(gp, S, bp) + teno_general<K, LIM>(vm, S, bm);
+  const unsigned flp = bp | ((unsigned)((ep - 7) & 3) << 6), flm = bm | ((unsigned)((em - 7) & 3) << 6);
+  const unsigned sm2 = (bp == all ? 1u : 0u) | (bm == all ? 2u : 0u);
+  fq[(NV + 2) * FQCAP + it] = f;
+  fq[(NV + 1) * FQCAP + it] = __longlong_as_double((long long)(flp | (flm << 8) | (sm2 << 16)));
+}
+
+/* The CTA's threads work through the items of every warp's queue together (wq_n[w] items
+   in warp w's queue at fq0 + w * FQCAP * fq_rows): item g goes to warp (g / 32 + rot) % W,
+   so a few items fill one warp's lanes instead of a few lanes of each warp (a partially
+   filled FP64 instruction occupies the FP64 pipe as long as a full one), and rot spreads
+   that warp over the SM's schedulers from one CTA to the next. */
+template <int NV, int K, int LIM, int AXIS, int LANES, int THREADS>
+__device__ __forceinline__ void field_queue_cta(const double* sm, int NP, double* fq0, const int* wq_n,
+                                                const SchemeDev& S, int& st, int rot) {
+  constexpr int W = THREADS / 32;
+  int pre[W + 1];
+  pre[0] = 0;
+#pragma unroll
+  for (int w = 0; w < W; ++w) pre[w + 1] = pre[w] + wq_n[w];
+  const int n = pre[W];
+  const int t = ((((int)threadIdx.x >> 5) + W - rot) % W) * 32 + ((int)threadIdx.x & 31);
+#pragma unroll 1
+  for (int g = t; g < n; g += THREADS) {
+    int w = 0;
+#pragma unroll
+    for (int v = 1; v < W; ++v) w += (g >= pre[v]) ? 1 : 0;
+    field_queue_item<NV, K, LIM, AXIS, LANES>(sm, NP, fq0 + (size_t)w * FQCAP * fq_rows<NV>(), g - pre[w], S, st);
   }
 }
 
@@ -137,62 +155,85 @@ __device__ __forceinline__ void stage_differences_fwd(const double* sm, float* s
 }
 
 /* Flux at the face whose K stencil points are the tile points (jf + q) * LANES + lane
-   (doubles sm, floats smf, NP points per component).  flags (may be null): NV x 2 bytes.
-   fq: this warp's field queue, shared by the lanes in am (all make this call). */
+   (doubles sm, floats smf, NP points per component), in steps so that the CTA can work
+   through the fields its warps queued together:
+     begin()     Roe average, LLF speeds, the central flux Fc;
+     fields()    per field the FP32 screen: central fields are done, the others are queued
+                 (returns false when the warp's queue is full before the last field: the
+                 caller flushes and calls it again);
+     readback()  after the CTA has processed the queues: the queued fields' flags and
+                 f+ + f- (or central after all);
+     finish()    the face flux.
+   flags (may be null): NV x 2 bytes.  fq: this warp's field queue, shared by the lanes in
+   am (all make each call). */
 template <int NV, int K, int LIM, int AXIS, int LANES>
-__device__ __forceinline__ void face_flux_fwd(const double* sm, const float* smf, int NP, int jf, int lane,
-                                              double gamma, const SchemeDev& sch, double (&Fh)[NV], uint8_t* flags,
-                                              int& st, double* fq, unsigned am) {
-  using L = PointLayoutF<NV>;
-  constexpr int D = NV - 2;
-  constexpr int H = K / 2;
-  constexpr unsigned all = (1u << (K - 2)) - 1u;
-  auto P = [&](int comp, int q) -> double { return sm[comp * NP + (jf + q) * LANES + lane]; };
-  auto Pf = [&](int comp, int q) -> float { return smf[comp * NP + (jf + q) * LANES + lane]; };
-  /* Roe average of cells f-1 (point H-1) and f (point H) */
-  const double sL = P(L::cS, H - 1), sR = P(L::cS, H);
-  const double wsum = rcp_nr(sL + sR);
-  double ut[D], q2 = 0.0;
+struct FwdFace {
+  static constexpr int D = NV - 2;
+  double ut[D], q2, Ht, cinv, ct, b1, b2, una, a_m, a_0, a_p;
+  double Fc[NV], fsv[NV];
+  unsigned cmask, qmask;
+  unsigned long long qslot;
+  int nq, s_next;
+
+  __device__ __forceinline__ void begin(const double* sm, int NP, int jf, int lane, double gamma, int& st) {
+    using L = PointLayoutF<NV>;
+    constexpr int H = K / 2;
+    auto P = [&](int comp, int q) -> double { return sm[comp * NP + (jf + q) * LANES + lane]; };
+    /* Roe average of cells f-1 (point H-1) and f (point H) */
+    const double sL = P(L::cS, H - 1), sR = P(L::cS, H);
+    const double wsum = rcp_nr(sL + sR);
+    q2 = 0.0;
 #pragma unroll
-  for (int d = 0; d < D; ++d) {
-    ut[d] = (sL * P(L::cV + d, H - 1) + sR * P(L::cV + d, H)) * wsum;
-    q2 += ut[d] * ut[d];
+    for (int d = 0; d < D; ++d) {
+      ut[d] = (sL * P(L::cV + d, H - 1) + sR * P(L::cV + d, H)) * wsum;
+      q2 += ut[d] * ut[d];
+    }
+    Ht = (sL * P(L::cH, H - 1) + sR * P(L::cH, H)) * wsum;
+    const double c2 = (gamma - 1.0) * (Ht - 0.5 * q2);
+    if (!ipos(c2)) st |= ST_ROE;
+    cinv = rsqrt_nr(c2);
+    ct = c2 * cinv;
+    b1 = (gamma - 1.0) * (cinv * cinv);
+    b2 = 0.5 * q2 * b1;
+    una = ut[AXIS];
+    /* LLF: alpha_s = max over the K stencil points of |lambda_s|, one per eigenvalue family */
+    a_m = 0.0;
+    a_0 = 0.0;
+    a_p = 0.0;
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      a_m = imax_nonneg(a_m, P(L::cLm, q));
+      a_0 = imax_nonneg(a_0, iabs(P(L::cV + AXIS, q)));
+      a_p = imax_nonneg(a_p, P(L::cLp, q));
+    }
+    /* Fc = sum_q c_q F(U_q), F = u_a U + p (e_{1+a} + u_a e_E) */
+    double cw[K];
+    central_weights<K>(cw);
+    double Pc = 0.0, PUc = 0.0;
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      Fc[v] = 0.0;
+      fsv[v] = 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const double cu = cw[q] * P(L::cV + AXIS, q);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Fc[v] = fma(cu, P(L::cU + v, q), Fc[v]);
+      Pc = fma(cw[q], P(L::cP, q), Pc);
+      PUc = fma(cu, P(L::cP, q), PUc);
+    }
+    Fc[1 + AXIS] += Pc;
+    Fc[NV - 1] += PUc;
+    cmask = 0u;
+    qmask = 0u;
+    qslot = 0ull;
+    nq = 0;
+    s_next = 0;
   }
-  const double Ht = (sL * P(L::cH, H - 1) + sR * P(L::cH, H)) * wsum;
-  const double c2 = (gamma - 1.0) * (Ht - 0.5 * q2);
-  if (!ipos(c2)) st |= ST_ROE;
-  const double cinv = rsqrt_nr(c2);
-  const double ct = c2 * cinv;
-  const double b1 = (gamma - 1.0) * (cinv * cinv);
-  const double b2 = 0.5 * q2 * b1;
-  const double una = ut[AXIS];
-  /* LLF: alpha_s = max over the K stencil points of |lambda_s|, one per eigenvalue family */
-  double a_m = 0.0, a_0 = 0.0, a_p = 0.0;
-#pragma unroll
-  for (int q = 0; q < K; ++q) {
-    a_m = imax_nonneg(a_m, P(L::cLm, q));
-    a_0 = imax_nonneg(a_0, iabs(P(L::cV + AXIS, q)));
-    a_p = imax_nonneg(a_p, P(L::cLp, q));
-  }
-  /* Fc = sum_q c_q F(U_q), F = u_a U + p (e_{1+a} + u_a e_E) */
-  double cw[K];
-  central_weights<K>(cw);
-  double Fc[NV], Pc = 0.0, PUc = 0.0;
-#pragma unroll
-  for (int v = 0; v < NV; ++v) Fc[v] = 0.0;
-#pragma unroll
-  for (int q = 0; q < K; ++q) {
-    const double cu = cw[q] * P(L::cV + AXIS, q);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) Fc[v] = fma(cu, P(L::cU + v, q), Fc[v]);
-    Pc = fma(cw[q], P(L::cP, q), Pc);
-    PUc = fma(cu, P(L::cP, q), PUc);
-  }
-  Fc[1 + AXIS] += Pc;
-  Fc[NV - 1] += PUc;
 
   /* left eigenvector l_s (closed form of R^{-1}) */
-  auto left_vector = [&](int s, double (&l)[NV]) {
+  __device__ __forceinline__ void left_vector(int s, double (&l)[NV]) const {
     const double sg = (s == 0) ? 1.0 : -1.0;            /* l: +1 for u-c, -1 for u+c */
     const int dt = (s - 2) < AXIS ? (s - 2) : (s - 1);  /* shear fields: tangential axes in increasing order */
     if ((s == 0) || (s == NV - 1)) {
@@ -214,20 +255,149 @@ __device__ __forceinline__ void face_flux_fwd(const double* sm, const float* smf
       for (int d = 0; d < D; ++d) l[1 + d] = (d == dt) ? 1.0 : 0.0;
       l[NV - 1] = 0.0;
     }
-  };
+  }
 
-  /* per field: central (bit s of cmask), else queued; fsv[s] receives f+ + f- of a queued
-     field that is not all smooth after all */
-  unsigned cmask = 0u, qmask = 0u;
-  unsigned long long qslot = 0ull;
-  int nq = 0;
-  double fsv[NV];
+  /* fields s_next.. : the FP32 screen decides which are central; the others are queued */
+  __device__ __forceinline__ bool fields(const float* smf, int NP, int jf, int lane, const SchemeDev& sch,
+                                         uint8_t* flags, double* fq, unsigned am) {
+    using L = PointLayoutF<NV>;
+    constexpr unsigned all = (1u << (K - 2)) - 1u;
+    auto Pf = [&](int comp, int q) -> float { return smf[comp * NP + (jf + q) * LANES + lane]; };
+    const float u32 = 5.9604645e-8f;
+#pragma unroll 1
+    for (int s = s_next; s < NV; ++s) {
+      const bool acoustic = (s == 0) || (s == NV - 1);
+      const int dt = (s - 2) < AXIS ? (s - 2) : (s - 1);
+      const bool shear = !acoustic && s != 1;
+      double l[NV];
+      left_vector(s, l);
+      const double ha = 0.5 * ((s == 0) ? a_m : (s == NV - 1 ? a_p : a_0));
+
+      /* --- FP32 screen.  With W_q = l.U_q, kappa_q = l_{1+a} + u_q l_E and G_q = u_q W_q +
+         p_q kappa_q, the differences of g+-_q = G_q/2 +- (alpha/2) W_q are, exactly,
+           D_t = (u_{t+1} dW_t + W_t du_t + p_{t+1} l_E du_t + kappa_t dp_t)/2 +- (alpha/2) dW_t
+         with dW_t = l.dU_t and dU, du, dp the FP64 differences of the point data (truncated
+         to FP32), so they are formed in FP32 to within 24 u of the magnitude of their terms,
+         A_t = (|u_{t+1}| dWA_t + WA_t |du_t| + |p_{t+1}| |l_E| |du_t| + |kappa_t| |dp_t|)/2 +
+         (alpha/2) dWA_t, dWA = |l|.|dU|, WA = |l|.|U| (inputs truncated to FP32, 2u each, at
+         most 5 terms per product sum) --- */
+      int exp_ = 7, exm_ = 7;
+      bool central = false;
+      if (!sch.exact_decisions && sch.default_d) {
+        float lf[NV], la[NV];
 #pragma unroll
-  for (int v = 0; v < NV; ++v) fsv[v] = 0.0;
-  auto flush = [&]() {
-    __syncwarp(am);
-    field_queue_process<NV, K, LIM, AXIS, LANES>(sm, NP, fq, nq, am, sch, st);
-    __syncwarp(am);
+        for (int v = 0; v < NV; ++v) {
+          lf[v] = f32_rz(l[v]);
+          la[v] = fabsf(lf[v]);
+        }
+        const float haf = f32_rz(ha);
+        float hdgv[K - 1], dwv[K - 1];  /* G differences / 2 and W differences */
+        float Am = 0.f;
+        float w0 = 0.f, wa0 = 0.f;  /* W and WA of point t */
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+          float w, wa;
+          if (shear) {
+            const float u0 = Pf(L::fU, q), ut1 = Pf(L::fU + 1 + dt, q);
+            w = fmaf(lf[0], u0, ut1);
+            wa = fmaf(la[0], fabsf(u0), fabsf(ut1));
+          } else {
+            w = lf[0] * Pf(L::fU, q);
+            wa = la[0] * fabsf(Pf(L::fU, q));
+#pragma unroll
+            for (int v = 1; v < NV; ++v) {
+              const float uv = Pf(L::fU + v, q);
+              w = fmaf(lf[v], uv, w);
+              wa = fmaf(la[v], fabsf(uv), wa);
+            }
+          }
+          if (q > 0) {
+            const int t = q - 1;  /* difference between points t and t + 1 = q */
+            float dw, dwa;
+            if (shear) {
+              const float d0 = Pf(L::fdU, t), d1 = Pf(L::fdU + 1 + dt, t);
+              dw = fmaf(lf[0], d0, d1);
+              dwa = fmaf(la[0], fabsf(d0), fabsf(d1));
+            } else {
+              dw = lf[0] * Pf(L::fdU, t);
+              dwa = la[0] * fabsf(Pf(L::fdU, t));
+#pragma unroll
+              for (int v = 1; v < NV; ++v) {
+                const float dv = Pf(L::fdU + v, t);
+                dw = fmaf(lf[v], dv, dw);
+                dwa = fmaf(la[v], fabsf(dv), dwa);
+              }
+            }
+            const float un1 = Pf(L::fN, q), p1 = Pf(L::fP, q), du = Pf(L::fdN, t);
+            float dg = fmaf(w0, du, un1 * dw);
+            float ag = fmaf(wa0, fabsf(du), fabsf(un1) * dwa);
+            if (!shear) {
+              const float kap = fmaf(Pf(L::fN, t), lf[NV - 1], lf[1 + AXIS]);
+              const float kapa = fmaf(fabsf(Pf(L::fN, t)), la[NV - 1], la[1 + AXIS]);
+              const float dpp = Pf(L::fdP, t);
+              dg = fmaf(p1 * lf[NV - 1], du, fmaf(kap, dpp, dg));
+              ag = fmaf(fabsf(p1) * la[NV - 1], fabsf(du), fmaf(kapa, fabsf(dpp), ag));
+            }
+            hdgv[t] = 0.5f * dg;
+            dwv[t] = dw;
+            Am = fmaxf(Am, fmaf(haf, dwa, 0.5f * ag));
+          }
+          w0 = w;
+          wa0 = wa;
+        }
+        const float Eb = 24.f * u32 * Am * (1.f + 4.f * u32) + 1e-30f;
+        const bool nex = flags != nullptr;
+        /* the two sides through one copy of the screen (a smaller loop body for the
+           instruction cache): f+ on d_t = dG_t/2 + (alpha/2) dW_t, f- on the stencil mirrored
+           about x_{i+1/2}, d_t = -(dG/2 - (alpha/2) dW)_{K-2-t} */
+        central = true;
+#pragma unroll 1
+        for (int side = 0; side < 2 && central; ++side) {
+          float d[K - 1], mx = 0.f;
+#pragma unroll
+          for (int t = 0; t < K - 1; ++t) {
+            d[t] = side ? -fmaf(-haf, dwv[K - 2 - t], hdgv[K - 2 - t]) : fmaf(haf, dwv[t], hdgv[t]);
+            mx = fmaxf(mx, fabsf(d[t]));
+          }
+          int ex_s = 7;
+          central = screen_smooth<K>(d, fmaf(2.f * u32, mx, Eb) * (1.f + 2.f * u32), sch, nex, ex_s);
+          if (side) exm_ = ex_s;
+          else exp_ = ex_s;
+        }
+      }
+      /* queue the field (l_s, alpha/2, header) when it is not certainly central; stop first
+         when the queue cannot take the warp's fields */
+      const unsigned lt = (1u << (threadIdx.x & 31u)) - 1u;
+      const unsigned mq = __ballot_sync(am, !central);
+      const int cnt = __popc(mq);
+      if (nq + cnt > FQCAP) {
+        s_next = s;  /* this field again after the flush (screened twice: rare) */
+        return false;
+      }
+      if (central) {
+        cmask |= 1u << s;
+        if (flags) {
+          flags[2 * s] = (uint8_t)(all | ((unsigned)(exp_ - 7) << 6));
+          flags[2 * s + 1] = (uint8_t)(all | ((unsigned)(exm_ - 7) << 6));
+        }
+      } else {
+        const int r = nq + __popc(mq & lt);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) fq[v * FQCAP + r] = l[v];
+        fq[NV * FQCAP + r] = ha;
+        fq[(NV + 1) * FQCAP + r] = __longlong_as_double((long long)(jf | (lane << 16) | (s << 21)));
+        qmask |= 1u << s;
+        qslot |= (unsigned long long)r << (7 * s);
+      }
+      nq += cnt;
+    }
+    s_next = NV;
+    return true;
+  }
+
+  /* after the CTA processed the queues: flags and f+ + f- of this face's queued fields; a
+     queued field found all smooth on both sides is central after all */
+  __device__ __forceinline__ void readback(const double* fq, uint8_t* flags, const SchemeDev& sch) {
 #pragma unroll
     for (int s = 0; s < NV; ++s)
       if (qmask >> s & 1u) {
@@ -237,188 +407,59 @@ __device__ __forceinline__ void face_flux_fwd(const double* sm, const float* smf
           flags[2 * s] = (uint8_t)(h & 0xff);
           flags[2 * s + 1] = (uint8_t)((h >> 8) & 0xff);
         }
-        if (((h >> 16) & 3u) == 3u && sch.default_d) cmask |= 1u << s;  /* all smooth after all */
+        if (((h >> 16) & 3u) == 3u && sch.default_d) cmask |= 1u << s;
         else fsv[s] = fq[(NV + 2) * FQCAP + r];
       }
     qmask = 0u;
     qslot = 0ull;
     nq = 0;
-    __syncwarp(am);  /* read back before the queue is refilled */
-  };
-
-  const float u32 = 5.9604645e-8f;
-  /* one pass per field, and a last pass (s == NV) that only flushes the queue: the queue
-     processing has a single call site (a smaller footprint in the instruction cache) */
-#pragma unroll 1
-  for (int s = 0; s <= NV; ++s) {
-    if (s == NV) {  /* the same in every lane */
-      if (nq > 0) flush();
-      break;
-    }
-    const bool acoustic = (s == 0) || (s == NV - 1);
-    const int dt = (s - 2) < AXIS ? (s - 2) : (s - 1);
-    const bool shear = !acoustic && s != 1;
-    double l[NV];
-    left_vector(s, l);
-    const double ha = 0.5 * ((s == 0) ? a_m : (s == NV - 1 ? a_p : a_0));
-
-    /* --- FP32 screen.  With W_q = l.U_q, kappa_q = l_{1+a} + u_q l_E and G_q = u_q W_q +
-       p_q kappa_q, the differences of g+-_q = G_q/2 +- (alpha/2) W_q are, exactly,
-         D_t = (u_{t+1} dW_t + W_t du_t + p_{t+1} l_E du_t + kappa_t dp_t)/2 +- (alpha/2) dW_t
-       with dW_t = l.dU_t and dU, du, dp the FP64 differences of the point data (truncated
-       to FP32), so they are formed in FP32 to within 24 u of the magnitude of their terms,
-       A_t = (|u_{t+1}| dWA_t + WA_t |du_t| + |p_{t+1}| |l_E| |du_t| + |kappa_t| |dp_t|)/2 +
-       (alpha/2) dWA_t, dWA = |l|.|dU|, WA = |l|.|U| (inputs truncated to FP32, 2u each, at
-       most 5 terms per product sum) --- */
-    int exp_ = 7, exm_ = 7;
-    bool central = false;
-    if (!sch.exact_decisions && sch.default_d) {
-      float lf[NV], la[NV];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        lf[v] = f32_rz(l[v]);
-        la[v] = fabsf(lf[v]);
-      }
-      const float haf = f32_rz(ha);
-      float hdgv[K - 1], dwv[K - 1];  /* G differences / 2 and W differences */
-      float Am = 0.f;
-      float w0 = 0.f, wa0 = 0.f;  /* W and WA of point t */
-#pragma unroll
-      for (int q = 0; q < K; ++q) {
-        float w, wa;
-        if (shear) {
-          const float u0 = Pf(L::fU, q), ut1 = Pf(L::fU + 1 + dt, q);
-          w = fmaf(lf[0], u0, ut1);
-          wa = fmaf(la[0], fabsf(u0), fabsf(ut1));
-        } else {
-          w = lf[0] * Pf(L::fU, q);
-          wa = la[0] * fabsf(Pf(L::fU, q));
-#pragma unroll
-          for (int v = 1; v < NV; ++v) {
-            const float uv = Pf(L::fU + v, q);
-            w = fmaf(lf[v], uv, w);
-            wa = fmaf(la[v], fabsf(uv), wa);
-          }
-        }
-        if (q > 0) {
-          const int t = q - 1;  /* difference between points t and t + 1 = q */
-          float dw, dwa;
-          if (shear) {
-            const float d0 = Pf(L::fdU, t), d1 = Pf(L::fdU + 1 + dt, t);
-            dw = fmaf(lf[0], d0, d1);
-            dwa = fmaf(la[0], fabsf(d0), fabsf(d1));
-          } else {
-            dw = lf[0] * Pf(L::fdU, t);
-            dwa = la[0] * fabsf(Pf(L::fdU, t));
-#pragma unroll
-            for (int v = 1; v < NV; ++v) {
-              const float dv = Pf(L::fdU + v, t);
-              dw = fmaf(lf[v], dv, dw);
-              dwa = fmaf(la[v], fabsf(dv), dwa);
-            }
-          }
-          const float un1 = Pf(L::fN, q), p1 = Pf(L::fP, q), du = Pf(L::fdN, t);
-          float dg = fmaf(w0, du, un1 * dw);
-          float ag = fmaf(wa0, fabsf(du), fabsf(un1) * dwa);
-          if (!shear) {
-            const float kap = fmaf(Pf(L::fN, t), lf[NV - 1], lf[1 + AXIS]);
-            const float kapa = fmaf(fabsf(Pf(L::fN, t)), la[NV - 1], la[1 + AXIS]);
-            const float dpp = Pf(L::fdP, t);
-            dg = fmaf(p1 * lf[NV - 1], du, fmaf(kap, dpp, dg));
-            ag = fmaf(fabsf(p1) * la[NV - 1], fabsf(du), fmaf(kapa, fabsf(dpp), ag));
-          }
-          hdgv[t] = 0.5f * dg;
-          dwv[t] = dw;
-          Am = fmaxf(Am, fmaf(haf, dwa, 0.5f * ag));
-        }
-        w0 = w;
-        wa0 = wa;
-      }
-      const float Eb = 24.f * u32 * Am * (1.f + 4.f * u32) + 1e-30f;
-      const bool nex = flags != nullptr;
-      /* the two sides through one copy of the screen (a smaller loop body for the
-         instruction cache): f+ on d_t = dG_t/2 + (alpha/2) dW_t, f- on the stencil mirrored
-         about x_{i+1/2}, d_t = -(dG/2 - (alpha/2) dW)_{K-2-t} */
-      central = true;
-#pragma unroll 1
-      for (int side = 0; side < 2 && central; ++side) {
-        float d[K - 1], mx = 0.f;
-#pragma unroll
-        for (int t = 0; t < K - 1; ++t) {
-          d[t] = side ? -fmaf(-haf, dwv[K - 2 - t], hdgv[K - 2 - t]) : fmaf(haf, dwv[t], hdgv[t]);
-          mx = fmaxf(mx, fabsf(d[t]));
-        }
-        int ex_s = 7;
-        central = screen_smooth<K>(d, fmaf(2.f * u32, mx, Eb) * (1.f + 2.f * u32), sch, nex, ex_s);
-        if (side) exm_ = ex_s;
-        else exp_ = ex_s;
-      }
-    }
-    if (central) {
-      cmask |= 1u << s;
-      if (flags) {
-        flags[2 * s] = (uint8_t)(all | ((unsigned)(exp_ - 7) << 6));
-        flags[2 * s + 1] = (uint8_t)(all | ((unsigned)(exm_ - 7) << 6));
-      }
-    }
-    /* queue the field (l_s, alpha/2, header) when it is not certainly central */
-    const unsigned lt = (1u << (threadIdx.x & 31u)) - 1u;
-    const unsigned mq = __ballot_sync(am, !central);
-    const int cnt = __popc(mq);
-    if (cnt == 0) continue;
-    if (nq + cnt > FQCAP) flush();
-    if (!central) {
-      const int r = nq + __popc(mq & lt);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) fq[v * FQCAP + r] = l[v];
-      fq[NV * FQCAP + r] = ha;
-      fq[(NV + 1) * FQCAP + r] = __longlong_as_double((long long)(jf | (lane << 16) | (s << 21)));
-      qmask |= 1u << s;
-      qslot |= (unsigned long long)r << (7 * s);
-    }
-    nq += cnt;
   }
 
-  constexpr unsigned allf = (1u << NV) - 1u;
-  if (cmask == allf) {
+  /* Fhat = Fc when every field is central, else sum_s r_s fs (right eigenvector r_s of
+     field s) with fs = l_s . Fc for the central fields */
+  __device__ __forceinline__ void finish(double (&Fh)[NV]) const {
+    constexpr unsigned allf = (1u << NV) - 1u;
+    if (cmask == allf) {
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Fh[v] = Fc[v];
-    return;
-  }
-  /* back-projection Fhat = sum_s r_s fs (right eigenvector r_s of field s) */
+      for (int v = 0; v < NV; ++v) Fh[v] = Fc[v];
+      return;
+    }
 #pragma unroll
-  for (int v = 0; v < NV; ++v) Fh[v] = 0.0;
+    for (int v = 0; v < NV; ++v) Fh[v] = 0.0;
 #pragma unroll 1
-  for (int s = 0; s < NV; ++s) {
-    double fs = fsv[s];
-    if (cmask >> s & 1u) {
-      double l[NV];
-      left_vector(s, l);
-      fs = l[0] * Fc[0];
+    for (int s = 0; s < NV; ++s) {
+      double fs = 0.0;
 #pragma unroll
-      for (int v = 1; v < NV; ++v) fs = fma(l[v], Fc[v], fs);
-    }
-    if ((s == 0) || (s == NV - 1)) {
-      const double sr = (s == 0) ? -1.0 : 1.0;         /* r: -c for u-c, +c for u+c */
-      Fh[0] += fs;
+      for (int v = 0; v < NV; ++v) fs = (v == s) ? fsv[v] : fs;
+      if (cmask >> s & 1u) {
+        double l[NV];
+        left_vector(s, l);
+        fs = l[0] * Fc[0];
 #pragma unroll
-      for (int d = 0; d < D; ++d) Fh[1 + d] += (ut[d] + (d == AXIS ? sr * ct : 0.0)) * fs;
-      Fh[NV - 1] += (Ht + sr * una * ct) * fs;
-    } else if (s == 1) {
-      Fh[0] += fs;
+        for (int v = 1; v < NV; ++v) fs = fma(l[v], Fc[v], fs);
+      }
+      if ((s == 0) || (s == NV - 1)) {
+        const double sr = (s == 0) ? -1.0 : 1.0;         /* r: -c for u-c, +c for u+c */
+        Fh[0] += fs;
 #pragma unroll
-      for (int d = 0; d < D; ++d) Fh[1 + d] += ut[d] * fs;
-      Fh[NV - 1] += 0.5 * q2 * fs;
-    } else {
-      const int dt = (s - 2) < AXIS ? (s - 2) : (s - 1);
+        for (int d = 0; d < D; ++d) Fh[1 + d] += (ut[d] + (d == AXIS ? sr * ct : 0.0)) * fs;
+        Fh[NV - 1] += (Ht + sr * una * ct) * fs;
+      } else if (s == 1) {
+        Fh[0] += fs;
 #pragma unroll
-      for (int d = 0; d < D; ++d)
-        if (d == dt) {
-          Fh[1 + d] += fs;
-          Fh[NV - 1] += ut[d] * fs;
-        }
+        for (int d = 0; d < D; ++d) Fh[1 + d] += ut[d] * fs;
+        Fh[NV - 1] += 0.5 * q2 * fs;
+      } else {
+        const int dt = (s - 2) < AXIS ? (s - 2) : (s - 1);
+#pragma unroll
+        for (int d = 0; d < D; ++d)
+          if (d == dt) {
+            Fh[1 + d] += fs;
+            Fh[NV - 1] += ut[d] * fs;
+          }
+      }
     }
   }
-}
+};
 
 }  // namespace tenom
