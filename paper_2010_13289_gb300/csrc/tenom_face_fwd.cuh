@@ -416,7 +416,14 @@ struct FwdFace {
   }
 
   /* Fhat = Fc when every field is central, else sum_s r_s fs (right eigenvector r_s of
-     field s) with fs = l_s . Fc for the central fields */
+     field s) with fs = l_s . Fc for the central fields.  Both sums go through the vectors
+     the eigenvectors share: a = (b2, -b1 u, b1) and b = cinv (u_a, -e_a, 0) give
+     l_{u-c} = (a + b)/2, l_{u+c} = (a - b)/2, l_entropy = e_0 - a, l_shear = e_{1+t} - u_t e_0,
+     and with sigma = f_{u-c} + f_{u+c}, delta = (f_{u+c} - f_{u-c}) c:
+       F_0 = sigma + f_1,  F_{1+d} = (sigma + f_1) u_d + (delta if d = a, else f_shear(d)),
+       F_E = sigma H + delta u_a + f_1 |u|^2/2 + sum_t f_t u_t
+     (the same sum as the back-projection term by term, in about a third of the FP64
+     operations: this runs in the lanes of the few faces that are not all central). */
   __device__ __forceinline__ void finish(double (&Fh)[NV]) const {
     constexpr unsigned allf = (1u << NV) - 1u;
     if (cmask == allf) {
@@ -424,41 +431,35 @@ struct FwdFace {
       for (int v = 0; v < NV; ++v) Fh[v] = Fc[v];
       return;
     }
+    double uF = 0.0;
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Fh[v] = 0.0;
-#pragma unroll 1
-    for (int s = 0; s < NV; ++s) {
-      double fs = 0.0;
+    for (int d = 0; d < D; ++d) uF = fma(ut[d], Fc[1 + d], uF);
+    const double A = fma(b2, Fc[0], b1 * (Fc[NV - 1] - uF));
+    const double B = cinv * fma(una, Fc[0], -Fc[1 + AXIS]);
+    double fs[NV];
+    fs[0] = (cmask & 1u) ? 0.5 * (A + B) : fsv[0];
+    fs[NV - 1] = (cmask >> (NV - 1) & 1u) ? 0.5 * (A - B) : fsv[NV - 1];
+    fs[1] = (cmask >> 1 & 1u) ? Fc[0] - A : fsv[1];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) fs = (v == s) ? fsv[v] : fs;
-      if (cmask >> s & 1u) {
-        double l[NV];
-        left_vector(s, l);
-        fs = l[0] * Fc[0];
-#pragma unroll
-        for (int v = 1; v < NV; ++v) fs = fma(l[v], Fc[v], fs);
-      }
-      if ((s == 0) || (s == NV - 1)) {
-        const double sr = (s == 0) ? -1.0 : 1.0;         /* r: -c for u-c, +c for u+c */
-        Fh[0] += fs;
-#pragma unroll
-        for (int d = 0; d < D; ++d) Fh[1 + d] += (ut[d] + (d == AXIS ? sr * ct : 0.0)) * fs;
-        Fh[NV - 1] += (Ht + sr * una * ct) * fs;
-      } else if (s == 1) {
-        Fh[0] += fs;
-#pragma unroll
-        for (int d = 0; d < D; ++d) Fh[1 + d] += ut[d] * fs;
-        Fh[NV - 1] += 0.5 * q2 * fs;
-      } else {
-        const int dt = (s - 2) < AXIS ? (s - 2) : (s - 1);
-#pragma unroll
-        for (int d = 0; d < D; ++d)
-          if (d == dt) {
-            Fh[1 + d] += fs;
-            Fh[NV - 1] += ut[d] * fs;
-          }
-      }
+    for (int s = 2; s <= NV - 2; ++s) {
+      const int dt = (s - 2) < AXIS ? (s - 2) : (s - 1);
+      fs[s] = (cmask >> s & 1u) ? fma(-ut[dt], Fc[0], Fc[1 + dt]) : fsv[s];
     }
+    const double sigma = fs[0] + fs[NV - 1];
+    const double delta = (fs[NV - 1] - fs[0]) * ct;
+    const double m = sigma + fs[1];
+    Fh[0] = m;
+    double FE = fma(sigma, Ht, fma(delta, una, 0.5 * q2 * fs[1]));
+#pragma unroll
+    for (int d = 0; d < D; ++d) Fh[1 + d] = m * ut[d];
+    Fh[1 + AXIS] += delta;
+#pragma unroll
+    for (int s = 2; s <= NV - 2; ++s) {
+      const int dt = (s - 2) < AXIS ? (s - 2) : (s - 1);
+      Fh[1 + dt] += fs[s];
+      FE = fma(ut[dt], fs[s], FE);
+    }
+    Fh[NV - 1] = FE;
   }
 };
 
