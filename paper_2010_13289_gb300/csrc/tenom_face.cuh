@@ -52,11 +52,14 @@ constexpr int FX_FACES = 128;  /* faces per CTA, x sweeps */
    the compiler room for ~168 registers (the halo rows cost little once the cell primitives
    come from the per-stage kernel) */
 __host__ __device__ constexpr int ft_faces(int K) { return (void)K, 4; }
-/* resident CTAs per SM the face kernels are compiled for: 3 x 128 threads leave 168
-   registers a thread (K = 8 with the deferred queue spills about 130 bytes a thread to
-   local memory at this budget and still runs 8 % faster on the 3D workload than with 214
-   registers at 2 CTAs per SM) */
-constexpr int FACE_CTAS_PER_SM = 3;
+/* resident CTAs per SM the face kernels are compiled for.  Forward kernels: 4 x 128
+   threads, 128 registers a thread (at most about 100 bytes of spills, at K = 8): where the
+   tile's shared memory allows a fourth CTA (2D, and every x sweep) the latency-bound
+   kernel gains more from it than it loses to the spills, and the 3D y/z sweeps (73 KB per
+   CTA, 3 CTAs) lose nothing.  Record and statistics kernels: 3 x 128 threads, 168
+   registers. */
+constexpr int FACE_CTAS_PER_SM = 4;
+constexpr int FACE_CTAS_PER_SM_REC = 3;
 
 template <int NV, int K, int AXIS>
 struct FaceTile {
@@ -506,7 +509,7 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
 }
 
 template <int NV, int K, int LIM, int AXIS, bool REC = false, bool STATS = false>
-__global__ void __launch_bounds__(FaceTile<NV, K, AXIS>::THREADS, FACE_CTAS_PER_SM)
+__global__ void __launch_bounds__(FaceTile<NV, K, AXIS>::THREADS, (REC || STATS) ? FACE_CTAS_PER_SM_REC : FACE_CTAS_PER_SM)
 face_kernel(const FaceArgs A) {
   using T = FaceTile<NV, K, AXIS>;
   constexpr int H = T::H;
