@@ -52,6 +52,10 @@ constexpr int FX_FACES = 128;  /* faces per CTA, x sweeps */
    the compiler room for ~168 registers (the halo rows cost little once the cell primitives
    come from the per-stage kernel) */
 __host__ __device__ constexpr int ft_faces(int K) { return (void)K, 4; }
+/* forward kernels, y/z sweeps: 16 x columns x 8 faces (a warp takes two face rows): with
+   K = 8 the tile stages 15 rows of 16 points for 128 faces instead of 11 rows of 32, so it
+   needs 1.9 staged points per face instead of 2.75 and fits 4 CTAs per SM in 3D */
+constexpr int FWD_LANES = 16;
 /* resident CTAs per SM the face kernels are compiled for.  Forward kernels: 4 x 128
    threads, 128 registers a thread (at most about 100 bytes of spills, at K = 8): where the
    tile's shared memory allows a fourth CTA (2D, and every x sweep) the latency-bound
@@ -61,12 +65,12 @@ __host__ __device__ constexpr int ft_faces(int K) { return (void)K, 4; }
 constexpr int FACE_CTAS_PER_SM = 4;
 constexpr int FACE_CTAS_PER_SM_REC = 3;
 
-template <int NV, int K, int AXIS>
+template <int NV, int K, int AXIS, bool FWDT = false>
 struct FaceTile {
   static constexpr int H = K / 2;
   static constexpr int NC = PointLayout<NV>::NC;
-  static constexpr int LANES = (AXIS == 0) ? 1 : 32;
-  static constexpr int FACES = (AXIS == 0) ? FX_FACES : ft_faces(K);
+  static constexpr int LANES = (AXIS == 0) ? 1 : (FWDT ? FWD_LANES : 32);
+  static constexpr int FACES = (AXIS == 0) ? FX_FACES : (FWDT ? 128 / FWD_LANES : ft_faces(K));
   static constexpr int ROWS = FACES + K - 1;     /* points along the axis */
   static constexpr int NP = ROWS * LANES;        /* points per tile */
   static constexpr int THREADS = FACES * LANES;
@@ -85,7 +89,7 @@ struct FaceTile {
 /* dynamic shared memory of face_kernel<..., REC, STATS, ...> */
 template <int NV, int K, int AXIS, bool REC, bool STATS>
 constexpr size_t face_smem() {
-  return (!REC && !STATS) ? FaceTile<NV, K, AXIS>::SMEM_FWD : FaceTile<NV, K, AXIS>::SMEM_Q;
+  return (!REC && !STATS) ? FaceTile<NV, K, AXIS, true>::SMEM_FWD : FaceTile<NV, K, AXIS>::SMEM_Q;
 }
 
 __device__ __forceinline__ int bc_wrap(int j, int n, int bc) {
@@ -509,9 +513,10 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
 }
 
 template <int NV, int K, int LIM, int AXIS, bool REC = false, bool STATS = false>
-__global__ void __launch_bounds__(FaceTile<NV, K, AXIS>::THREADS, (REC || STATS) ? FACE_CTAS_PER_SM_REC : FACE_CTAS_PER_SM)
+__global__ void __launch_bounds__(FaceTile<NV, K, AXIS, !REC && !STATS>::THREADS,
+                                  (REC || STATS) ? FACE_CTAS_PER_SM_REC : FACE_CTAS_PER_SM)
 face_kernel(const FaceArgs A) {
-  using T = FaceTile<NV, K, AXIS>;
+  using T = FaceTile<NV, K, AXIS, !REC && !STATS>;
   constexpr int H = T::H;
   extern __shared__ double sm[];
   const int tid = threadIdx.x;
@@ -525,7 +530,7 @@ face_kernel(const FaceArgs A) {
     o2 = row / A.n[1];
     f0 = blockIdx.y * T::FACES;
   } else {
-    x0 = blockIdx.x * 32;
+    x0 = blockIdx.x * T::LANES;
     f0 = blockIdx.y * T::FACES;
     o2 = blockIdx.z;                     /* AXIS 1: z ; AXIS 2: y */
   }
@@ -537,8 +542,8 @@ face_kernel(const FaceArgs A) {
   float* smf = reinterpret_cast<float*>(sm + (size_t)T::NCF * T::NP + T::FQDOUBLES);  /* forward kernels */
   int st = 0;
   for (int p = tid; p < T::NP; p += T::THREADS) {
-    const int lane = (AXIS == 0) ? 0 : (p & 31);
-    const int row = (AXIS == 0) ? p : (p >> 5);
+    const int lane = (AXIS == 0) ? 0 : (p % T::LANES);
+    const int row = (AXIS == 0) ? p : (p / T::LANES);
     const int j = bc_wrap(f0 - H + row, na, A.bc[AXIS]);
     long long base;
     if (AXIS == 0) base = sy * o1 + sz * o2;
@@ -583,8 +588,8 @@ face_kernel(const FaceArgs A) {
   }
 
   /* --- phase 2: one face per thread --- */
-  const int lane = (AXIS == 0) ? 0 : (tid & 31);
-  const int jf = (AXIS == 0) ? tid : (tid >> 5);
+  const int lane = (AXIS == 0) ? 0 : (tid % T::LANES);
+  const int jf = (AXIS == 0) ? tid : (tid / T::LANES);
   const int f = f0 + jf;
   const int xg = x0 + lane;
   /* forward kernels on a periodic axis compute faces 0 .. n-1 only: face n has the same

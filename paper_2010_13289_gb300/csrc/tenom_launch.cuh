@@ -40,11 +40,12 @@ static cudaError_t ensure_smem_attr(Kern kern, AttrOnce& attr, size_t smem) {
 
 template <class Kern>
 static cudaError_t launch_tile(Kern kern, AttrOnce& attr, size_t smem, int nv, int axis, const int* n, int K,
-                               cudaStream_t st, const void* args_ptr, bool wrapped = false) {
+                               cudaStream_t st, const void* args_ptr, bool wrapped = false,
+                               bool fwd_tile = false) {
   cudaError_t e = ensure_smem_attr(kern, attr, smem);
   if (e != cudaSuccess) return e;
   dim3 grid, block;
-  face_grid(nv, axis, n, K, &grid, &block, wrapped);
+  face_grid(nv, axis, n, K, &grid, &block, wrapped, fwd_tile);
   void* argv[1] = {const_cast<void*>(args_ptr)};
   return cudaLaunchKernel((const void*)kern, grid, block, argv, smem, st);
 }
@@ -55,7 +56,7 @@ template <int NV, int K, int LIM, int AXIS, bool REC, bool STATS>
 static cudaError_t launch_face_one(const FaceArgs& a, cudaStream_t st) {
   static AttrOnce attr;
   return launch_tile(face_kernel<NV, K, LIM, AXIS, REC, STATS>, attr, face_smem<NV, K, AXIS, REC, STATS>(), NV, AXIS,
-                     a.n, K, st, &a, !REC && !STATS && a.bc[AXIS] == 0);
+                     a.n, K, st, &a, !REC && !STATS && a.bc[AXIS] == 0, !REC && !STATS);
 }
 
 template <int NV, int AXIS, bool REC, bool STATS>
