@@ -106,8 +106,10 @@ static StageFn pick_stage(int K, int lim, int tile, bool pp) {
   return nullptr;
 }
 
+/* dynamic shared memory of the stage kernel of (K, tile): the kernel's own layout */
 static size_t stage_smem(int K, int tile) {
-  return sizeof(double) * (PointLayout<3>::NC * (tile + K - 1) + 3 * tile);
+  if (K == 6) return tile == 64 ? BatchTile<6, 64>::SMEM : (tile == 128 ? BatchTile<6, 128>::SMEM : BatchTile<6, 256>::SMEM);
+  return tile == 64 ? BatchTile<8, 64>::SMEM : (tile == 128 ? BatchTile<8, 128>::SMEM : BatchTile<8, 256>::SMEM);
 }
 
 }  // namespace tenom
