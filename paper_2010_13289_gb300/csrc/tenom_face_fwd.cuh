@@ -86,7 +86,7 @@ __device__ __forceinline__ void field_queue_item(const double* sm, int NP, doubl
   const int dt = (s - 2) < AXIS ? (s - 2) : (s - 1);
   const bool shear = s >= 2 && s <= NV - 2;
   auto P = [&](int comp, int q) -> double { return sm[comp * NP + (jf + q) * LANES + ln]; };
-  double gp[K], gm[K];
+  double wv[K], hgv[K];
 #pragma unroll
   for (int q = 0; q < K; ++q) {
     const double un = P(L::cV + AXIS, q), pq = P(L::cP, q);
@@ -100,18 +100,32 @@ __device__ __forceinline__ void field_queue_item(const double* sm, int NP, doubl
       for (int v = 1; v < NV; ++v) w = fma(l[v], P(L::cU + v, q), w);
       kap = fma(un, l[NV - 1], l[1 + AXIS]);
     }
-    const double hg = 0.5 * fma(pq, kap, un * w);  /* G/2 = (u_a W + p kappa)/2 */
-    gp[q] = fma(ha, w, hg);
-    gm[q] = fma(-ha, w, hg);
+    wv[q] = w;
+    hgv[q] = 0.5 * fma(pq, kap, un * w);  /* G/2 = (u_a W + p kappa)/2 */
   }
-  double vm[K];
-#pragma unroll
-  for (int q = 0; q < K; ++q) vm[q] = gm[K - 1 - q];  /* f- on the stencil mirrored about x_{i+1/2} */
+  /* the two split sides through one copy of the decisions and the reconstruction:
+     f+ on g+_q = G_q/2 + (alpha/2) W_q, f- on g-_q = G_q/2 - (alpha/2) W_q mirrored about
+     x_{i+1/2} */
   unsigned bp = 0, bm = 0;
   int ep = 7, em = 7;
-  if (!teno_decide_fast<K>(gp, S, bp, ep)) teno_decide_fp64<K>(gp, S, bp, ep, st);
-  if (!teno_decide_fast<K>(vm, S, bm, em)) teno_decide_fp64<K>(vm, S, bm, em, st);
-  const double f = teno_general<K, LIM>(gp, S, bp) + teno_general<K, LIM>(vm, S, bm);
+  double f = 0.0;
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {
+    double v[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) v[q] = side ? fma(-ha, wv[K - 1 - q], hgv[K - 1 - q]) : fma(ha, wv[q], hgv[q]);
+    unsigned b = 0;
+    int e = 7;
+    if (!teno_decide_fast<K>(v, S, b, e)) teno_decide_fp64<K>(v, S, b, e, st);
+    f += teno_general<K, LIM>(v, S, b);
+    if (side) {
+      bm = b;
+      em = e;
+    } else {
+      bp = b;
+      ep = e;
+    }
+  }
   const unsigned flp = bp | ((unsigned)((ep - 7) & 3) << 6), flm = bm | ((unsigned)((em - 7) & 3) << 6);
   const unsigned sm2 = (bp == all ? 1u : 0u) | (bm == all ? 2u : 0u);
   fq[(NV + 2) * FQCAP + it] = f;
