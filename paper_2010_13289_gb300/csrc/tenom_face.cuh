@@ -56,14 +56,12 @@ __host__ __device__ constexpr int ft_faces(int K) { return (void)K, 4; }
    K = 8 the tile stages 15 rows of 16 points for 128 faces instead of 11 rows of 32, so it
    needs 1.9 staged points per face instead of 2.75 and fits 4 CTAs per SM in 3D */
 constexpr int FWD_LANES = 16;
-/* resident CTAs per SM the face kernels are compiled for.  Forward kernels: 4 x 128
-   threads, 128 registers a thread (at most about 100 bytes of spills, at K = 8): where the
-   tile's shared memory allows a fourth CTA (2D, and every x sweep) the latency-bound
-   kernel gains more from it than it loses to the spills, and the 3D y/z sweeps (73 KB per
-   CTA, 3 CTAs) lose nothing.  Record and statistics kernels: 3 x 128 threads, 168
-   registers. */
+/* resident CTAs per SM the face kernels are compiled for.  Forward and record kernels: 4 x
+   128 threads, 128 registers a thread (at most about 100 bytes of spills, at K = 8): the
+   latency-bound kernel gains more from the fourth CTA than it loses to the spills.
+   Statistics kernels: 3 x 128 threads, 168 registers. */
 constexpr int FACE_CTAS_PER_SM = 4;
-constexpr int FACE_CTAS_PER_SM_REC = 3;
+constexpr int FACE_CTAS_PER_SM_STATS = 3;
 
 template <int NV, int K, int AXIS, bool FWDT = false>
 struct FaceTile {
@@ -89,7 +87,7 @@ struct FaceTile {
 /* dynamic shared memory of face_kernel<..., REC, STATS, ...> */
 template <int NV, int K, int AXIS, bool REC, bool STATS>
 constexpr size_t face_smem() {
-  return (!REC && !STATS) ? FaceTile<NV, K, AXIS, true>::SMEM_FWD : FaceTile<NV, K, AXIS>::SMEM_Q;
+  return !STATS ? FaceTile<NV, K, AXIS, true>::SMEM_FWD : FaceTile<NV, K, AXIS>::SMEM_Q;
 }
 
 __device__ __forceinline__ int bc_wrap(int j, int n, int bc) {
@@ -513,10 +511,10 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
 }
 
 template <int NV, int K, int LIM, int AXIS, bool REC = false, bool STATS = false>
-__global__ void __launch_bounds__(FaceTile<NV, K, AXIS, !REC && !STATS>::THREADS,
-                                  (REC || STATS) ? FACE_CTAS_PER_SM_REC : FACE_CTAS_PER_SM)
+__global__ void __launch_bounds__(FaceTile<NV, K, AXIS, !STATS>::THREADS,
+                                  STATS ? FACE_CTAS_PER_SM_STATS : FACE_CTAS_PER_SM)
 face_kernel(const FaceArgs A) {
-  using T = FaceTile<NV, K, AXIS, !REC && !STATS>;
+  using T = FaceTile<NV, K, AXIS, !STATS>;
   constexpr int H = T::H;
   extern __shared__ double sm[];
   const int tid = threadIdx.x;
@@ -538,7 +536,7 @@ face_kernel(const FaceArgs A) {
   const long long sa = (AXIS == 0) ? sx : (AXIS == 1 ? sy : sz);
 
   /* --- phase 1: point quantities --- */
-  constexpr bool FWD = !REC && !STATS;
+  constexpr bool FWD = !STATS;  /* forward and record kernels: the screened face flux */
   float* smf = reinterpret_cast<float*>(sm + (size_t)T::NCF * T::NP + T::FQDOUBLES);  /* forward kernels */
   int st = 0;
   for (int p = tid; p < T::NP; p += T::THREADS) {
@@ -595,7 +593,7 @@ face_kernel(const FaceArgs A) {
   /* forward kernels on a periodic axis compute faces 0 .. n-1 only: face n has the same
      stencil points as face 0, and face 0's lanes write it to both places (face_grid sizes
      those launches for n faces, which drops the nearly empty last tile of every line) */
-  const bool wrapped = FWD && A.bc[AXIS] == 0;
+  const bool wrapped = FWD && !REC && A.bc[AXIS] == 0;
   bool active = (wrapped ? f < na : f <= na) && (AXIS == 0 || xg < A.n[0]);
   const unsigned am = __ballot_sync(0xffffffffu, active);  /* the lanes sharing the warp's queue */
   unsigned cnt[STATS ? SC_COUNT : 1];
@@ -614,8 +612,15 @@ face_kernel(const FaceArgs A) {
     constexpr int W = T::THREADS / 32;
     double* const fq0 = sm + (size_t)T::NCF * T::NP;
     double* const fq = fq0 + (size_t)(tid >> 5) * FQCAP * fq_rows<NV>();
-    FwdFace<NV, K, LIM, AXIS, T::LANES> F;
+    FwdFace<NV, K, LIM, AXIS, T::LANES, REC> F;
     if (active) F.begin(sm, T::NP, jf, lane, A.gamma, st);
+    /* record kernels: the tape row of the face in tile row r, x column x0 + c */
+    auto tape = [&](int r, int c) -> double* {
+      const long long fr = f0 + r, xr = x0 + c;
+      if (AXIS == 0) return A.lin + fr + (long long)(A.n[0] + 1) * (o1 + (long long)A.n[1] * o2);
+      if (AXIS == 1) return A.lin + xr + (long long)A.n[0] * (fr + (long long)(A.n[1] + 1) * o2);
+      return A.lin + xr + (long long)A.n[0] * (o2 + (long long)A.n[1] * fr);
+    };
     const int rot = (int)((blockIdx.x + blockIdx.y + blockIdx.z) % W);
     bool again = true;
 #pragma unroll 1
@@ -623,13 +628,14 @@ face_kernel(const FaceArgs A) {
       bool stopped = false;
       int mine = 0;
       if (active && F.s_next < NV) {
-        stopped = !F.fields(smf, T::NP, jf, lane, A.sch, flg, fq, am);
+        stopped = !F.fields(smf, T::NP, jf, lane, A.sch, flg, fq, am, REC ? A.lin + flin : nullptr, A.nface);
         mine = F.nq;
       }
       const int wn = __reduce_max_sync(0xffffffffu, mine);
       if ((tid & 31) == 0) wq_n[tid >> 5] = wn;
       __syncthreads();
-      field_queue_cta<NV, K, LIM, AXIS, T::LANES, T::THREADS>(sm, T::NP, fq0, wq_n, A.sch, st, rot);
+      field_queue_cta<NV, K, LIM, AXIS, T::LANES, T::THREADS, REC>(sm, T::NP, fq0, wq_n, A.sch, st, rot, tape,
+                                                                   A.nface);
       again = __syncthreads_or(stopped);
       if (active) F.readback(fq, flg, A.sch);
     }

@@ -24,6 +24,7 @@
  * G = l . F(U) = u_n (l . U) + p (l_{1+a} + u_n l_E).
  */
 #pragma once
+#include <cstddef>
 #include "tenom_recon.cuh"
 #include "tenom_queue.cuh"
 
@@ -71,10 +72,12 @@ template <int NV>
 __host__ __device__ constexpr int fq_rows() { return NV + 3; }
 
 /* one queued field: FP64 projection of its K points, decisions of both split sides
-   (certified FP32 filter, else FP64), reconstruction; result and flags into its slot */
-template <int NV, int K, int LIM, int AXIS, int LANES>
+   (certified FP32 filter, else FP64), reconstruction; result and flags into its slot.
+   REC: also the field's linearisation (the record kernels' tape row, see face_flux_smem)
+   at tape(row, lane) + s (2K + 2) lstride. */
+template <int NV, int K, int LIM, int AXIS, int LANES, bool REC, class Tape>
 __device__ __forceinline__ void field_queue_item(const double* sm, int NP, double* fq, int it, const SchemeDev& S,
-                                                 int& st) {
+                                                 int& st, const Tape& tape, long long lstride) {
   using L = PointLayoutF<NV>;
   constexpr unsigned all = (1u << (K - 2)) - 1u;
   const long long h = __double_as_longlong(fq[(NV + 1) * FQCAP + it]);
@@ -109,6 +112,7 @@ __device__ __forceinline__ void field_queue_item(const double* sm, int NP, doubl
   unsigned bp = 0, bm = 0;
   int ep = 7, em = 7;
   double f = 0.0;
+  double op[REC ? K : 1], om[REC ? K : 1];  /* frozen linear weights of f+ and f- */
 #pragma unroll 1
   for (int side = 0; side < 2; ++side) {
     double v[K];
@@ -117,7 +121,17 @@ __device__ __forceinline__ void field_queue_item(const double* sm, int NP, doubl
     unsigned b = 0;
     int e = 7;
     if (!teno_decide_fast<K>(v, S, b, e)) teno_decide_fp64<K>(v, S, b, e, st);
-    f += teno_general<K, LIM>(v, S, b);
+    if constexpr (REC) {
+      double wt[K];
+      f += teno_general<K, LIM, true>(v, S, b, wt);
+#pragma unroll
+      for (int q = 0; q < K; ++q) {
+        if (side) om[q] = wt[q];
+        else op[q] = wt[q];
+      }
+    } else {
+      f += teno_general<K, LIM>(v, S, b);
+    }
     if (side) {
       bm = b;
       em = e;
@@ -130,6 +144,21 @@ __device__ __forceinline__ void field_queue_item(const double* sm, int NP, doubl
   const unsigned sm2 = (bp == all ? 1u : 0u) | (bm == all ? 2u : 0u);
   fq[(NV + 2) * FQCAP + it] = f;
   fq[(NV + 1) * FQCAP + it] = __longlong_as_double((long long)(flp | (flm << 8) | (sm2 << 16)));
+  if constexpr (REC) {
+    /* fs = sum_q sigma_q G_q + (alpha/2) delta_q W_q with sigma_q = (op_q + om_{K-1-q})/2,
+       delta_q = op_q - om_{K-1-q}; omegaW = sum_q delta_q W_q */
+    double* o = tape(jf, ln) + (long long)s * (2 * K + 2) * lstride;
+    double wW = 0.0;
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      const double dq = op[q] - om[K - 1 - q];
+      o[(2 + q) * lstride] = 0.5 * (op[q] + om[K - 1 - q]);
+      o[(2 + K + q) * lstride] = dq;
+      wW = fma(dq, wv[q], wW);
+    }
+    o[0] = f;
+    o[lstride] = wW;
+  }
 }
 
 /* The CTA's threads work through the items of every warp's queue together (wq_n[w] items
@@ -137,9 +166,10 @@ __device__ __forceinline__ void field_queue_item(const double* sm, int NP, doubl
    so a few items fill one warp's lanes instead of a few lanes of each warp (a partially
    filled FP64 instruction occupies the FP64 pipe as long as a full one), and rot spreads
    that warp over the SM's schedulers from one CTA to the next. */
-template <int NV, int K, int LIM, int AXIS, int LANES, int THREADS>
+template <int NV, int K, int LIM, int AXIS, int LANES, int THREADS, bool REC = false, class Tape = std::nullptr_t>
 __device__ __forceinline__ void field_queue_cta(const double* sm, int NP, double* fq0, const int* wq_n,
-                                                const SchemeDev& S, int& st, int rot) {
+                                                const SchemeDev& S, int& st, int rot, const Tape& tape = nullptr,
+                                                long long lstride = 0) {
   constexpr int W = THREADS / 32;
   int pre[W + 1];
   pre[0] = 0;
@@ -152,7 +182,8 @@ __device__ __forceinline__ void field_queue_cta(const double* sm, int NP, double
     int w = 0;
 #pragma unroll
     for (int v = 1; v < W; ++v) w += (g >= pre[v]) ? 1 : 0;
-    field_queue_item<NV, K, LIM, AXIS, LANES>(sm, NP, fq0 + (size_t)w * FQCAP * fq_rows<NV>(), g - pre[w], S, st);
+    field_queue_item<NV, K, LIM, AXIS, LANES, REC>(sm, NP, fq0 + (size_t)w * FQCAP * fq_rows<NV>(), g - pre[w], S, st,
+                                                   tape, lstride);
   }
 }
 
@@ -180,7 +211,7 @@ __device__ __forceinline__ void stage_differences_fwd(const double* sm, float* s
      finish()    the face flux.
    flags (may be null): NV x 2 bytes.  fq: this warp's field queue, shared by the lanes in
    am (all make each call). */
-template <int NV, int K, int LIM, int AXIS, int LANES>
+template <int NV, int K, int LIM, int AXIS, int LANES, bool REC = false>
 struct FwdFace {
   static constexpr int D = NV - 2;
   double ut[D], q2, Ht, cinv, ct, b1, b2, una, a_m, a_0, a_p;
@@ -273,7 +304,8 @@ struct FwdFace {
 
   /* fields s_next.. : the FP32 screen decides which are central; the others are queued */
   __device__ __forceinline__ bool fields(const float* smf, int NP, int jf, int lane, const SchemeDev& sch,
-                                         uint8_t* flags, double* fq, unsigned am) {
+                                         uint8_t* flags, double* fq, unsigned am, double* lin = nullptr,
+                                         long long lstride = 0) {
     using L = PointLayoutF<NV>;
     constexpr unsigned all = (1u << (K - 2)) - 1u;
     auto Pf = [&](int comp, int q) -> float { return smf[comp * NP + (jf + q) * LANES + lane]; };
@@ -393,6 +425,21 @@ struct FwdFace {
         if (flags) {
           flags[2 * s] = (uint8_t)(all | ((unsigned)(exp_ - 7) << 6));
           flags[2 * s + 1] = (uint8_t)(all | ((unsigned)(exm_ - 7) << 6));
+        }
+        if constexpr (REC) {  /* both sides central: op = om = the central weights c */
+          double cw[K];
+          central_weights<K>(cw);
+          double* o = lin + (long long)s * (2 * K + 2) * lstride;
+#pragma unroll
+          for (int q = 0; q < K; ++q) {
+            o[(2 + q) * lstride] = 0.5 * (cw[q] + cw[K - 1 - q]);
+            o[(2 + K + q) * lstride] = cw[q] - cw[K - 1 - q];
+          }
+          double fs = l[0] * Fc[0];
+#pragma unroll
+          for (int v = 1; v < NV; ++v) fs = fma(l[v], Fc[v], fs);
+          o[0] = fs;
+          o[lstride] = 0.0;
         }
       } else {
         const int r = nq + __popc(mq & lt);
