@@ -52,7 +52,7 @@ ADJOINT_DEFAULT = "adjoint_broadband_2d_512_teno6_mp"
 FP64_LANES_PER_CLK = 304  # FP64 pipe: 2 lanes per clock per SM x 152 SMs
 
 
-FACE_SOURCES = ("tenom_face.cuh", "tenom_face_fwd.cuh", "tenom_queue.cuh", "tenom_recon.cuh", "tenom_linear.cuh",
+FACE_SOURCES = ("tenom_face.cuh", "tenom_face_fwd.cuh", "tenom_recon.cuh", "tenom_linear.cuh",
                 "tenom_stats.cuh", "teno_coeffs.cuh", "tenom_fastmath.cuh", "tenom_launch.cuh", "tenom_internal.h")
 
 

@@ -18,7 +18,6 @@
 #include "tenom_linear.cuh"
 #include "tenom_stats.cuh"
 #include "tenom_fastmath.cuh"
-#include "tenom_queue.cuh"
 #include "tenom_face_fwd.cuh"
 
 namespace tenom {
@@ -73,9 +72,6 @@ struct FaceTile {
   static constexpr int NP = ROWS * LANES;        /* points per tile */
   static constexpr int THREADS = FACES * LANES;
   static constexpr size_t SMEM = sizeof(double) * NC * NP;
-  /* + one reconstruction queue per warp (recon_pair_queued) */
-  static constexpr size_t QDOUBLES = (size_t)(THREADS / 32) * QSLOTS * (K + 2);
-  static constexpr size_t SMEM_Q = SMEM + sizeof(double) * QDOUBLES;
   /* forward kernels (face_flux_fwd): their point layout, one field queue per warp, then
      the FP32 copies of the point data */
   static constexpr int NCF = PointLayoutF<NV>::NC;
@@ -87,7 +83,7 @@ struct FaceTile {
 /* dynamic shared memory of face_kernel<..., REC, STATS, ...> */
 template <int NV, int K, int AXIS, bool REC, bool STATS>
 constexpr size_t face_smem() {
-  return !STATS ? FaceTile<NV, K, AXIS, true>::SMEM_FWD : FaceTile<NV, K, AXIS>::SMEM_Q;
+  return !STATS ? FaceTile<NV, K, AXIS, true>::SMEM_FWD : FaceTile<NV, K, AXIS>::SMEM;
 }
 
 __device__ __forceinline__ int bc_wrap(int j, int n, int bc) {
@@ -152,96 +148,16 @@ __device__ __forceinline__ void stage_point(const double (&u)[NV], double gamma,
   stage_point_from<NV, AXIS>(u, vel, pr, Hh, c, sr, sm, NP, p);
 }
 
-template <int K, int LIM, bool WT>
-__device__ __forceinline__ void recon_pair_queued(const double (&vp)[K], const double (&vm)[K], const SchemeDev& S,
-                                                  double* wq, unsigned am, double& fp, double& fm, unsigned& flp,
-                                                  unsigned& flm, double* wp, double* wm, int& st) {
-  constexpr unsigned all = (1u << (K - 2)) - 1u;
-  constexpr long long DECIDED = 0x100;
-  unsigned bp = 0, bm = 0;
-  int ep = 7, em = 7;
-  const bool cp = teno_decide_fast<K>(vp, S, bp, ep);
-  const bool cm = teno_decide_fast<K>(vm, S, bm, em);
-  flp = bp | ((unsigned)((ep - 7) & 3) << 6);
-  flm = bm | ((unsigned)((em - 7) & 3) << 6);
-  const bool centp = cp && bp == all && S.default_d, centm = cm && bm == all && S.default_d;
-  fp = 0.0;
-  fm = 0.0;
-  if (centp) fp = teno_central<K, WT>(vp, wp);
-  if (centm) fm = teno_central<K, WT>(vm, wm);
-  const unsigned lane = threadIdx.x & 31u, lt = (1u << lane) - 1u;
-  __syncwarp(am);  /* the previous field's results have been read back */
-  const unsigned mp = __ballot_sync(am, !centp), mm = __ballot_sync(am, !centm);
-  const int np = __popc(mp), n = np + __popc(mm);
-  if (n == 0) return;
-  const int rp = __popc(mp & lt), rm = np + __popc(mm & lt);
-  if (!centp) {
-#pragma unroll
-    for (int q = 0; q < K; ++q) wq[q * QSLOTS + rp] = vp[q];
-    wq[(K + 1) * QSLOTS + rp] = __longlong_as_double(cp ? (DECIDED | flp) : 0ll);
-  }
-  if (!centm) {
-#pragma unroll
-    for (int q = 0; q < K; ++q) wq[q * QSLOTS + rm] = vm[q];
-    wq[(K + 1) * QSLOTS + rm] = __longlong_as_double(cm ? (DECIDED | flm) : 0ll);
-  }
-  __syncwarp(am);
-  const int wl = __popc(am & lt), na = __popc(am);
-  for (int base = 0; base < n; base += na) {
-    const int it = base + wl;
-    if (it < n) {
-      double v[K];
-#pragma unroll
-      for (int q = 0; q < K; ++q) v[q] = wq[q * QSLOTS + it];
-      const long long h = __double_as_longlong(wq[(K + 1) * QSLOTS + it]);
-      unsigned bits = (unsigned)h & 63u;
-      int ex = 7 + (int)((h >> 6) & 3);
-      if (!(h & DECIDED)) teno_decide_fp64<K>(v, S, bits, ex, st);
-      double w[WT ? K : 1];
-      const double f = teno_general<K, LIM, WT>(v, S, bits, w);
-      wq[K * QSLOTS + it] = f;
-      wq[(K + 1) * QSLOTS + it] = __longlong_as_double((long long)(bits | ((unsigned)((ex - 7) & 3) << 6)));
-      if constexpr (WT) {
-#pragma unroll
-        for (int q = 0; q < K; ++q) wq[q * QSLOTS + it] = w[q];
-      }
-    }
-  }
-  __syncwarp(am);
-  if (!centp) {
-    fp = wq[K * QSLOTS + rp];
-    flp = (unsigned)__double_as_longlong(wq[(K + 1) * QSLOTS + rp]);
-    if constexpr (WT) {
-#pragma unroll
-      for (int q = 0; q < K; ++q) wp[q] = wq[q * QSLOTS + rp];
-    }
-  }
-  if (!centm) {
-    fm = wq[K * QSLOTS + rm];
-    flm = (unsigned)__double_as_longlong(wq[(K + 1) * QSLOTS + rm]);
-    if constexpr (WT) {
-#pragma unroll
-      for (int q = 0; q < K; ++q) wm[q] = wq[q * QSLOTS + rm];
-    }
-  }
-}
-
 /* Flux at the face whose K stencil points are shared-memory points (jf + q) * LANES + lane,
    q = 0..K-1, of a tile laid out by PointLayout<NV> with NP points per component:
    Roe average of points K/2-1 and K/2, characteristic projection, LLF split, TENO-M per
-   field and side, back-projection.  flags (may be null) receives NV x 2 bytes.
-   REC: also write the face's linearisation to lin[j * lstride], j = s * (2K + 2) + ...:
-   per characteristic field s the reconstructed fs = f+ + f-, omegaW = sum_q delta_q W_q,
-   sigma_q (K) and delta_q (K), where with the frozen linear weights op (f+) and om (f-, on
-   the mirrored stencil) fs = sum_q sigma_q G_q + (alpha_s/2) delta_q W_q:
-   sigma_q = (op_q + om_{K-1-q})/2, delta_q = op_q - om_{K-1-q}.
-   wq (may be null): this warp's reconstruction queue (recon_pair_queued), shared by the
-   lanes in am, which must all make this call; null: each lane reconstructs its own sides. */
-template <int NV, int K, int LIM, int AXIS, int LANES, bool REC = false, bool STATS = false>
+   field and side (each lane its own), back-projection.  flags (may be null) receives NV x 2
+   bytes.  The batched stage kernel's face flux; STATS: the decision statistics of both
+   sides of every field into cnt (SC_COUNT counters) instead of the flux. */
+template <int NV, int K, int LIM, int AXIS, int LANES, bool STATS = false>
 __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf, int lane, double gamma,
                                                const SchemeDev& sch, double (&Fh)[NV], uint8_t* flags, int& st,
-                                               double* lin = nullptr, long long lstride = 0, double* wq = nullptr,
-                                               unsigned am = 0u, unsigned* cnt = nullptr) {
+                                               unsigned* cnt = nullptr) {
   using L = PointLayout<NV>;
   constexpr int D = NV - 2;
   constexpr int H = K / 2;
@@ -299,41 +215,12 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
         }
     }
   };
-  /* Deferred warp queue (forward without recording): the sides that need the general
-     reconstruction are collected over all fields (flushed early only when full) and worked
-     through together; their back-projection and flags follow the flush.  Per (field, side)
-     entry e = 2s + side: qmask bit e, queue index in 6-bit field e of qslot. */
-  constexpr bool DQ = !REC && !STATS;
-  unsigned qmask = 0u;
-  unsigned long long qslot = 0ull;
-  int nq = 0;
-  double fsr[DQ ? NV : 1];  /* fs per field, back-projected in field order after the last flush */
-#pragma unroll
-  for (int v = 0; v < (DQ ? NV : 1); ++v) fsr[v] = 0.0;
-  auto flush = [&]() {
-    __syncwarp(am);
-    queue_process<K, LIM>(wq, nq, am, sch, st);
-    __syncwarp(am);
-#pragma unroll
-    for (int e = 0; e < 2 * NV; ++e)
-      if (qmask >> e & 1u) {
-        const int r = (int)((qslot >> (6 * e)) & 63ull);
-        if constexpr (DQ) fsr[e >> 1] += wq[K * QSLOTS + r];
-        if (flags) flags[e] = (uint8_t)__double_as_longlong(wq[(K + 1) * QSLOTS + r]);
-      }
-    qmask = 0u;
-    qslot = 0ull;
-    nq = 0;
-    __syncwarp(am);  /* read back before the queue is refilled */
-  };
-
-  /* Forward without recording: the acoustic pair and the entropy field share the vectors
-     a = (b2, -b1 u, b1) and b = (u_n / c, -e_n / c, 0): l_{u-+c} = (a +- b)/2, l_0 = e_0 - a.
-     Per stencil point A = a.U/2, B = b.U/2, AF = a.F/4, BF = b.F/4 once, then
-     W_{u-+c} = A +- B, G_{u-+c}/2 = AF +- BF, W_0 = rho - 2A, G_0/2 = F_rho/2 - 2AF. */
-  constexpr bool SH = K == 6 || !REC;  /* recording with K = 8: the arrays cost more occupancy than they save */
-  double pA[SH ? K : 1], pB[SH ? K : 1], pAF[SH ? K : 1], pBF[SH ? K : 1];
-  if constexpr (SH) {
+  /* The acoustic pair and the entropy field share the vectors a = (b2, -b1 u, b1) and
+     b = (u_n / c, -e_n / c, 0): l_{u-+c} = (a +- b)/2, l_0 = e_0 - a.  Per stencil point
+     A = a.U/2, B = b.U/2, AF = a.F/4, BF = b.F/4 once, then W_{u-+c} = A +- B,
+     G_{u-+c}/2 = AF +- BF, W_0 = rho - 2A, G_0/2 = F_rho/2 - 2AF. */
+  double pA[K], pB[K], pAF[K], pBF[K];
+  {
     double ah[NV], aq[NV];
     ah[0] = 0.5 * b2;
 #pragma unroll
@@ -386,36 +273,20 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
     /* characteristic projection of the K stencil points and LLF split
        g+- = (G +- alpha W)/2, evaluated as fma(+-alpha/2, W, G/2) */
     const double ha = 0.5 * ((s == 0) ? a_m : (s == NV - 1 ? a_p : a_0));
-    double gp[K], gm[K], Wr[REC ? K : 1];
-    if (SH && acoustic) {
+    double gp[K], gm[K];
+    if (acoustic) {
 #pragma unroll
       for (int q = 0; q < K; ++q) {
         const double w = fma(sg, pB[q], pA[q]), hg = fma(sg, pBF[q], pAF[q]);
         gp[q] = fma(ha, w, hg);
         gm[q] = fma(-ha, w, hg);
-        if constexpr (REC) Wr[q] = w;
       }
-    } else if (SH && s == 1) {
+    } else if (s == 1) {
 #pragma unroll
       for (int q = 0; q < K; ++q) {
         const double w = fma(-2.0, pA[q], P(L::cU, q)), hg = fma(-2.0, pAF[q], 0.5 * P(L::cF, q));
         gp[q] = fma(ha, w, hg);
         gm[q] = fma(-ha, w, hg);
-        if constexpr (REC) Wr[q] = w;
-      }
-    } else if (acoustic || s == 1) {
-#pragma unroll
-      for (int q = 0; q < K; ++q) {
-        double w = l[0] * P(L::cU, q), g = l[0] * P(L::cF, q);
-#pragma unroll
-        for (int v = 1; v < NV; ++v) {
-          w = fma(l[v], P(L::cU + v, q), w);
-          g = fma(l[v], P(L::cF + v, q), g);
-        }
-        const double hg = 0.5 * g;
-        gp[q] = fma(ha, w, hg);
-        gm[q] = fma(-ha, w, hg);
-        if constexpr (REC) Wr[q] = w;
       }
     } else {
       /* shear wave: l = (-u_t, e_t, 0) */
@@ -425,7 +296,6 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
         const double hg = 0.5 * fma(-utt, P(L::cF, q), P(L::cF + 1 + dt, q));
         gp[q] = fma(ha, w, hg);
         gm[q] = fma(-ha, w, hg);
-        if constexpr (REC) Wr[q] = w;
       }
     }
     /* f+ on the upwind stencil, f- on the stencil mirrored about x_{i+1/2} */
@@ -438,75 +308,13 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
       continue;
     }
     unsigned flp, flm;
-    double op[REC ? K : 1], om[REC ? K : 1];
-    double fplus, fminus;
-    if (DQ && wq) {
-      /* certified decisions and central sides in the lane; the rest to the queue */
-      constexpr unsigned all = (1u << (K - 2)) - 1u;
-      unsigned bp = 0, bm = 0;
-      int ep = 7, em = 7;
-      const bool cp = teno_decide_fast<K>(gp, sch, bp, ep);
-      const bool cm = teno_decide_fast<K>(vm, sch, bm, em);
-      const bool centp = cp && bp == all && sch.default_d, centm = cm && bm == all && sch.default_d;
-      fplus = centp ? teno_central<K>(gp) : 0.0;
-      fminus = centm ? teno_central<K>(vm) : 0.0;
-      flp = bp | ((unsigned)((ep - 7) & 3) << 6);
-      flm = bm | ((unsigned)((em - 7) & 3) << 6);
-      if (flags) {
-        if (centp) flags[s * 2 + 0] = (uint8_t)flp;
-        if (centm) flags[s * 2 + 1] = (uint8_t)flm;
-      }
-      const unsigned lt = (1u << (threadIdx.x & 31u)) - 1u;
-      const unsigned mp = __ballot_sync(am, !centp), mm = __ballot_sync(am, !centm);
-      const int cnt = __popc(mp) + __popc(mm);
-      if (nq + cnt > QSLOTS) flush();
-      const int rp = nq + __popc(mp & lt), rm = nq + __popc(mp) + __popc(mm & lt);
-      if (!centp) {
-        queue_put<K>(wq, rp, gp, cp, flp);
-        qmask |= 1u << (2 * s);
-        qslot |= (unsigned long long)rp << (12 * s);
-      }
-      if (!centm) {
-        queue_put<K>(wq, rm, vm, cm, flm);
-        qmask |= 2u << (2 * s);
-        qslot |= (unsigned long long)rm << (12 * s + 6);
-      }
-      nq += cnt;
-    } else if (wq) {
-      recon_pair_queued<K, LIM, REC>(gp, vm, sch, wq, am, fplus, fminus, flp, flm, op, om, st);
-    } else {
-      fplus = teno_m<K, LIM, REC>(gp, sch, flp, st, op);
-      fminus = teno_m<K, LIM, REC>(vm, sch, flm, st, om);
-    }
-    if (flags && !(DQ && wq)) {
+    const double fplus = teno_m<K, LIM>(gp, sch, flp, st);
+    const double fminus = teno_m<K, LIM>(vm, sch, flm, st);
+    if (flags) {
       flags[s * 2 + 0] = (uint8_t)flp;
       flags[s * 2 + 1] = (uint8_t)flm;
     }
-    const double fs = fplus + fminus;
-    if (DQ && wq) {
-      if constexpr (DQ) fsr[s] = fs;  /* central sides now, queued sides at the flush */
-      continue;
-    }
-    if constexpr (REC) {
-      double* o = lin + (long long)s * (2 * K + 2) * lstride;
-      double wW = 0.0;
-#pragma unroll
-      for (int q = 0; q < K; ++q) {
-        const double dq = op[q] - om[K - 1 - q];
-        o[(2 + q) * lstride] = 0.5 * (op[q] + om[K - 1 - q]);
-        o[(2 + K + q) * lstride] = dq;
-        wW = fma(dq, Wr[q], wW);
-      }
-      o[0] = fs;
-      o[lstride] = wW;
-    }
-    backproj(s, fs);
-  }
-  if (DQ && wq) {
-    if (nq > 0) flush();
-#pragma unroll
-    for (int s = 0; s < NV; ++s)
-      if constexpr (DQ) backproj(s, fsr[s]);
+    backproj(s, fplus + fminus);
   }
 }
 
@@ -643,9 +451,7 @@ face_kernel(const FaceArgs A) {
   }
   if (active) {
     if constexpr (!FWD)
-      face_flux_smem<NV, K, LIM, AXIS, T::LANES, REC, STATS>(
-          sm, T::NP, jf, lane, A.gamma, A.sch, Fh, flg, st, REC ? A.lin + flin : nullptr, A.nface,
-          sm + T::NC * T::NP + (size_t)(tid >> 5) * QSLOTS * (K + 2), am, cnt);
+      face_flux_smem<NV, K, LIM, AXIS, T::LANES, STATS>(sm, T::NP, jf, lane, A.gamma, A.sch, Fh, flg, st, cnt);
     if constexpr (!STATS) {
 #pragma unroll
       for (int v = 0; v < NV; ++v) A.Fhat[v * A.nface + flin] = Fh[v];

@@ -26,7 +26,6 @@
 #pragma once
 #include <cstddef>
 #include "tenom_recon.cuh"
-#include "tenom_queue.cuh"
 
 namespace tenom {
 
