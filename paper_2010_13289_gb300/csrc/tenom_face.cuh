@@ -47,6 +47,9 @@ struct PointLayout {
 };
 
 constexpr int FX_FACES = 128;  /* faces per CTA, x sweeps */
+/* forward and record kernels, x sweeps: 256 faces per CTA for K = 8 (one CTA queue over 8
+   warps, 7 halo points per 256 faces), 128 for K = 6 */
+__host__ __device__ constexpr int fx_faces(int K) { return K == 8 ? 256 : 128; }
 /* faces per CTA along the axis, y/z sweeps (x 32 lanes): 4, i.e. 128-thread CTAs that leave
    the compiler room for ~168 registers (the halo rows cost little once the cell primitives
    come from the per-stage kernel) */
@@ -55,11 +58,11 @@ __host__ __device__ constexpr int ft_faces(int K) { return (void)K, 4; }
    K = 8 the tile stages 15 rows of 16 points for 128 faces instead of 11 rows of 32, so it
    needs 1.9 staged points per face instead of 2.75 and fits 4 CTAs per SM in 3D */
 constexpr int FWD_LANES = 16;
-/* resident CTAs per SM the face kernels are compiled for.  Forward and record kernels: 4 x
-   128 threads, 128 registers a thread (at most about 100 bytes of spills, at K = 8): the
-   latency-bound kernel gains more from the fourth CTA than it loses to the spills.
-   Statistics kernels: 3 x 128 threads, 168 registers. */
-constexpr int FACE_CTAS_PER_SM = 4;
+/* resident threads per SM the forward and record kernels are compiled for: 512 (4 CTAs of
+   128 threads or 2 of 256), 128 registers a thread (at most about 100 bytes of spills, at
+   K = 8): the latency-bound kernel gains more from the fourth group of warps than it loses
+   to the spills.  Statistics kernels: 3 CTAs of 128 threads, 168 registers. */
+constexpr int FACE_THREADS_PER_SM = 512;
 constexpr int FACE_CTAS_PER_SM_STATS = 3;
 
 template <int NV, int K, int AXIS, bool FWDT = false>
@@ -67,7 +70,7 @@ struct FaceTile {
   static constexpr int H = K / 2;
   static constexpr int NC = PointLayout<NV>::NC;
   static constexpr int LANES = (AXIS == 0) ? 1 : (FWDT ? FWD_LANES : 32);
-  static constexpr int FACES = (AXIS == 0) ? FX_FACES : (FWDT ? 128 / FWD_LANES : ft_faces(K));
+  static constexpr int FACES = (AXIS == 0) ? (FWDT ? fx_faces(K) : FX_FACES) : (FWDT ? 128 / FWD_LANES : ft_faces(K));
   static constexpr int ROWS = FACES + K - 1;     /* points along the axis */
   static constexpr int NP = ROWS * LANES;        /* points per tile */
   static constexpr int THREADS = FACES * LANES;
@@ -320,7 +323,7 @@ __device__ __forceinline__ void face_flux_smem(const double* sm, int NP, int jf,
 
 template <int NV, int K, int LIM, int AXIS, bool REC = false, bool STATS = false>
 __global__ void __launch_bounds__(FaceTile<NV, K, AXIS, !STATS>::THREADS,
-                                  STATS ? FACE_CTAS_PER_SM_STATS : FACE_CTAS_PER_SM)
+                                  STATS ? FACE_CTAS_PER_SM_STATS : FACE_THREADS_PER_SM / FaceTile<NV, K, AXIS, !STATS>::THREADS)
 face_kernel(const FaceArgs A) {
   using T = FaceTile<NV, K, AXIS, !STATS>;
   constexpr int H = T::H;
@@ -401,7 +404,7 @@ face_kernel(const FaceArgs A) {
   /* forward kernels on a periodic axis compute faces 0 .. n-1 only: face n has the same
      stencil points as face 0, and face 0's lanes write it to both places (face_grid sizes
      those launches for n faces, which drops the nearly empty last tile of every line) */
-  const bool wrapped = FWD && !REC && A.bc[AXIS] == 0;
+  const bool wrapped = FWD && A.bc[AXIS] == 0;
   bool active = (wrapped ? f < na : f <= na) && (AXIS == 0 || xg < A.n[0]);
   const unsigned am = __ballot_sync(0xffffffffu, active);  /* the lanes sharing the warp's queue */
   unsigned cnt[STATS ? SC_COUNT : 1];
@@ -465,6 +468,10 @@ face_kernel(const FaceArgs A) {
         if (A.flags) {
 #pragma unroll
           for (int e = 0; e < 2 * NV; ++e) A.flags[fn * NV * 2 + e] = A.flags[flin * NV * 2 + e];
+        }
+        if constexpr (REC) {  /* the tape rows, complete after the last queue round's barrier */
+#pragma unroll 1
+          for (int r = 0; r < NV * (2 * K + 2); ++r) A.lin[r * A.nface + fn] = A.lin[r * A.nface + flin];
         }
       }
     }

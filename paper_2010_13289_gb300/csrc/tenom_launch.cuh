@@ -56,7 +56,7 @@ template <int NV, int K, int LIM, int AXIS, bool REC, bool STATS>
 static cudaError_t launch_face_one(const FaceArgs& a, cudaStream_t st) {
   static AttrOnce attr;
   return launch_tile(face_kernel<NV, K, LIM, AXIS, REC, STATS>, attr, face_smem<NV, K, AXIS, REC, STATS>(), NV, AXIS,
-                     a.n, K, st, &a, !REC && !STATS && a.bc[AXIS] == 0, !STATS);
+                     a.n, K, st, &a, !STATS && a.bc[AXIS] == 0, !STATS);
 }
 
 template <int NV, int AXIS, bool REC, bool STATS>
