@@ -47,16 +47,17 @@ struct PointLayout {
 };
 
 constexpr int FX_FACES = 128;  /* faces per CTA, x sweeps */
-/* forward and record kernels, x sweeps: 256 faces per CTA for K = 8 (one CTA queue over 8
-   warps, 7 halo points per 256 faces), 128 for K = 6 */
+/* threads (faces) per CTA of the forward and record kernels: 256 for K = 8 (one CTA queue
+   over 8 warps, fewer halo points per face: x sweeps 256 faces of a row, y/z sweeps 16 x
+   columns by 16 faces), 128 for K = 6 */
 __host__ __device__ constexpr int fx_faces(int K) { return K == 8 ? 256 : 128; }
 /* faces per CTA along the axis, y/z sweeps (x 32 lanes): 4, i.e. 128-thread CTAs that leave
    the compiler room for ~168 registers (the halo rows cost little once the cell primitives
    come from the per-stage kernel) */
 __host__ __device__ constexpr int ft_faces(int K) { return (void)K, 4; }
-/* forward kernels, y/z sweeps: 16 x columns x 8 faces (a warp takes two face rows): with
-   K = 8 the tile stages 15 rows of 16 points for 128 faces instead of 11 rows of 32, so it
-   needs 1.9 staged points per face instead of 2.75 and fits 4 CTAs per SM in 3D */
+/* forward and record kernels, y/z sweeps: FWD_LANES x columns by fx_faces(K) / FWD_LANES
+   faces (a warp takes two face rows): with K = 8 the tile stages 23 rows of 16 points for
+   256 faces (1.4 staged points per face; 11 rows of 32 for 128 faces were 2.75) */
 constexpr int FWD_LANES = 16;
 /* resident threads per SM the forward and record kernels are compiled for: 512 (4 CTAs of
    128 threads or 2 of 256), 128 registers a thread (at most about 100 bytes of spills, at
@@ -70,7 +71,7 @@ struct FaceTile {
   static constexpr int H = K / 2;
   static constexpr int NC = PointLayout<NV>::NC;
   static constexpr int LANES = (AXIS == 0) ? 1 : (FWDT ? FWD_LANES : 32);
-  static constexpr int FACES = (AXIS == 0) ? (FWDT ? fx_faces(K) : FX_FACES) : (FWDT ? 128 / FWD_LANES : ft_faces(K));
+  static constexpr int FACES = (AXIS == 0) ? (FWDT ? fx_faces(K) : FX_FACES) : (FWDT ? fx_faces(K) / FWD_LANES : ft_faces(K));
   static constexpr int ROWS = FACES + K - 1;     /* points along the axis */
   static constexpr int NP = ROWS * LANES;        /* points per tile */
   static constexpr int THREADS = FACES * LANES;

@@ -34,7 +34,7 @@ inline void face_grid(int nv, int axis, const int* n, int K, dim3* grid, dim3* b
   } else {
     const int other = (axis == 1) ? n[2] : n[1];
     const int lanes = fwd_tile ? FWD_LANES : 32;
-    const int ft = fwd_tile ? 128 / FWD_LANES : ft_faces(K);
+    const int ft = fwd_tile ? fx_faces(K) / FWD_LANES : ft_faces(K);
     *block = dim3(lanes * ft);
     *grid = dim3((unsigned)((n[0] + lanes - 1) / lanes), (unsigned)((nf + ft - 1) / ft), (unsigned)other);
   }
