@@ -47,15 +47,16 @@ struct PointLayout {
 };
 
 constexpr int FX_FACES = 128;  /* faces per CTA, x sweeps */
-/* threads (faces) per CTA of the forward and record kernels: 256 for K = 8 (one CTA queue
-   over 8 warps, fewer halo points per face: x sweeps 256 faces of a row, y/z sweeps 16 x
-   columns by 16 faces), 128 for K = 6 */
-__host__ __device__ constexpr int fx_faces(int K) { return K == 8 ? 256 : 128; }
+/* threads (faces) per CTA of the forward and record kernels: 256 for K = 8 in 2D and 3D
+   (one CTA queue over 8 warps, fewer halo points per face: x sweeps 256 faces of a row,
+   y/z sweeps 16 x columns by 16 faces), 128 for K = 6 and for 1D grids (a short line is
+   latency-bound: it runs faster spread over more, smaller CTAs) */
+__host__ __device__ constexpr int fx_faces(int K, int NV) { return (K == 8 && NV > 3) ? 256 : 128; }
 /* faces per CTA along the axis, y/z sweeps (x 32 lanes): 4, i.e. 128-thread CTAs that leave
    the compiler room for ~168 registers (the halo rows cost little once the cell primitives
    come from the per-stage kernel) */
 __host__ __device__ constexpr int ft_faces(int K) { return (void)K, 4; }
-/* forward and record kernels, y/z sweeps: FWD_LANES x columns by fx_faces(K) / FWD_LANES
+/* forward and record kernels, y/z sweeps: FWD_LANES x columns by fx_faces(K, NV) / FWD_LANES
    faces (a warp takes two face rows): with K = 8 the tile stages 23 rows of 16 points for
    256 faces (1.4 staged points per face; 11 rows of 32 for 128 faces were 2.75) */
 constexpr int FWD_LANES = 16;
@@ -71,7 +72,7 @@ struct FaceTile {
   static constexpr int H = K / 2;
   static constexpr int NC = PointLayout<NV>::NC;
   static constexpr int LANES = (AXIS == 0) ? 1 : (FWDT ? FWD_LANES : 32);
-  static constexpr int FACES = (AXIS == 0) ? (FWDT ? fx_faces(K) : FX_FACES) : (FWDT ? fx_faces(K) / FWD_LANES : ft_faces(K));
+  static constexpr int FACES = (AXIS == 0) ? (FWDT ? fx_faces(K, NV) : FX_FACES) : (FWDT ? fx_faces(K, NV) / FWD_LANES : ft_faces(K));
   static constexpr int ROWS = FACES + K - 1;     /* points along the axis */
   static constexpr int NP = ROWS * LANES;        /* points per tile */
   static constexpr int THREADS = FACES * LANES;

@@ -21,20 +21,19 @@ cudaError_t launch_stats_nv5(const FaceArgs& a, int axis, int K, int lim, cudaSt
 /* Launch geometry of a face sweep (kept in one place for the tests of the host logic):
    tiles over the n_a + 1 faces of a line, or over n_a faces (wrapped: a forward kernel on
    a periodic axis, whose face n_a is face 0's copy); fwd_tile: the forward and record
-   kernels' tiles (fx_faces(K) along x; FWD_LANES x columns in y/z), else FX_FACES along x
+   kernels' tiles (fx_faces(K, nv) along x; FWD_LANES x columns in y/z), else FX_FACES along x
    and 32 x columns x ft_faces(K). */
 inline void face_grid(int nv, int axis, const int* n, int K, dim3* grid, dim3* block, bool wrapped = false,
                       bool fwd_tile = false) {
-  (void)nv;
   const int nf = n[axis] + (wrapped ? 0 : 1);
   if (axis == 0) {
-    const int fx = fwd_tile ? fx_faces(K) : FX_FACES;
+    const int fx = fwd_tile ? fx_faces(K, nv) : FX_FACES;
     *block = dim3(fx);
     *grid = dim3((unsigned)(n[1] * n[2]), (unsigned)((nf + fx - 1) / fx));
   } else {
     const int other = (axis == 1) ? n[2] : n[1];
     const int lanes = fwd_tile ? FWD_LANES : 32;
-    const int ft = fwd_tile ? fx_faces(K) / FWD_LANES : ft_faces(K);
+    const int ft = fwd_tile ? fx_faces(K, nv) / FWD_LANES : ft_faces(K);
     *block = dim3(lanes * ft);
     *grid = dim3((unsigned)((n[0] + lanes - 1) / lanes), (unsigned)((nf + ft - 1) / ft), (unsigned)other);
   }
