@@ -7,8 +7,8 @@
  *   rebuilds its frozen linear reconstructions and writes its K x NV point adjoints to its
  *   own shared-memory slots, then each staged point gathers the slots of the faces that
  *   touch it and adds the sum to Z.
- * adj_lin_kernel: from the linearisation the forward recorded (face_flux_smem, REC); see
- *   the comment above it.
+ * adj_lin_kernel: from the linearisation the record kernels wrote (field_queue_item in
+ *   tenom_face_fwd.cuh gives the tape layout); see the comment above it.
  * Z is updated with atomics: halo points are shared with the neighbouring tiles and
  * boundary ghosts fold onto their cell. */
 #pragma once

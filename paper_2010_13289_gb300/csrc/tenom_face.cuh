@@ -2,15 +2,17 @@
  * characteristic decomposition, Rusanov / local Lax-Friedrichs splitting, TENO-M per
  * characteristic field and split side, back-projection).
  *
- * One CTA owns a tile of consecutive faces along the sweep axis:
- *   axis x : 128 faces of one row, one thread per face (x is contiguous);
- *   axis y,z: 32 contiguous x-columns (lanes) x FT faces along the axis (warps).
+ * One CTA owns a tile of consecutive faces along the sweep axis, one thread per face:
+ *   axis x : a run of faces of one row (x is contiguous);
+ *   axis y,z: contiguous x-columns (lanes) x faces along the axis.
+ * (Tile sizes: FaceTile; forward and record kernels use fx_faces / FWD_LANES.)
  * Phase 1 stages the tile's points (faces + K-1 halo points, boundary condition applied
- * at load: periodic wrap or zero-gradient clamp) and computes every point quantity once
- * into shared memory: U, the physical flux F_a(U), velocity, total enthalpy H, sound
- * speed c and sqrt(rho).  Phase 2 computes each face flux exactly once and writes it to
- * the face buffer [nvar][nface_a]; the cell update (flux difference) reads it later, so
- * both neighbouring cells use the same face value.
+ * at load: periodic wrap or zero-gradient clamp) with every point quantity they need,
+ * once, in shared memory (U, velocity, H, sqrt(rho), p, |u -+ c|; the forward and record
+ * kernels add FP32 copies and differences for the screen, tenom_face_fwd.cuh).  Phase 2
+ * computes each face flux exactly once and writes it to the face buffer [nvar][nface_a];
+ * the cell update (flux difference) reads it later, so both neighbouring cells use the
+ * same face value.
  */
 #pragma once
 #include <cstdint>
@@ -52,9 +54,8 @@ constexpr int FX_FACES = 128;  /* faces per CTA, x sweeps */
    y/z sweeps 16 x columns by 16 faces), 128 for K = 6 and for 1D grids (a short line is
    latency-bound: it runs faster spread over more, smaller CTAs) */
 __host__ __device__ constexpr int fx_faces(int K, int NV) { return (K == 8 && NV > 3) ? 256 : 128; }
-/* faces per CTA along the axis, y/z sweeps (x 32 lanes): 4, i.e. 128-thread CTAs that leave
-   the compiler room for ~168 registers (the halo rows cost little once the cell primitives
-   come from the per-stage kernel) */
+/* faces per CTA along the axis of the statistics kernels and the adjoint sweeps, y/z
+   (x 32 lanes): 4, i.e. 128-thread CTAs */
 __host__ __device__ constexpr int ft_faces(int K) { return (void)K, 4; }
 /* forward and record kernels, y/z sweeps: FWD_LANES x columns by fx_faces(K, NV) / FWD_LANES
    faces (a warp takes two face rows): with K = 8 the tile stages 23 rows of 16 points for
@@ -77,15 +78,15 @@ struct FaceTile {
   static constexpr int NP = ROWS * LANES;        /* points per tile */
   static constexpr int THREADS = FACES * LANES;
   static constexpr size_t SMEM = sizeof(double) * NC * NP;
-  /* forward kernels (face_flux_fwd): their point layout, one field queue per warp, then
-     the FP32 copies of the point data */
+  /* forward and record kernels (FwdFace): their point layout, one field queue per warp,
+     then the FP32 copies of the point data and the queue lengths */
   static constexpr int NCF = PointLayoutF<NV>::NC;
   static constexpr size_t FQDOUBLES = (size_t)(THREADS / 32) * FQCAP * fq_rows<NV>();
   static constexpr size_t SMEM_FWD = sizeof(double) * ((size_t)NCF * NP + FQDOUBLES) +
                                      sizeof(float) * (size_t)PointLayoutF<NV>::NF * NP + sizeof(int) * (THREADS / 32);
 };
 
-/* dynamic shared memory of face_kernel<..., REC, STATS, ...> */
+/* dynamic shared memory of face_kernel<..., REC, STATS> */
 template <int NV, int K, int AXIS, bool REC, bool STATS>
 constexpr size_t face_smem() {
   return !STATS ? FaceTile<NV, K, AXIS, true>::SMEM_FWD : FaceTile<NV, K, AXIS>::SMEM;

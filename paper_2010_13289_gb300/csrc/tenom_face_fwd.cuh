@@ -72,8 +72,12 @@ __host__ __device__ constexpr int fq_rows() { return NV + 3; }
 
 /* one queued field: FP64 projection of its K points, decisions of both split sides
    (certified FP32 filter, else FP64), reconstruction; result and flags into its slot.
-   REC: also the field's linearisation (the record kernels' tape row, see face_flux_smem)
-   at tape(row, lane) + s (2K + 2) lstride. */
+   REC: also the field's linearisation at tape(row, lane) + s (2K + 2) lstride.  The record
+   kernels' tape, per face and characteristic field s, rows j = s (2K + 2) + ... with stride
+   lstride (the number of faces): the reconstructed fs = f+ + f-, omegaW = sum_q delta_q W_q,
+   sigma_q (K) and delta_q (K), where with the frozen linear weights op (f+) and om (f-, on
+   the mirrored stencil) fs = sum_q sigma_q G_q + (alpha_s/2) delta_q W_q:
+   sigma_q = (op_q + om_{K-1-q})/2, delta_q = op_q - om_{K-1-q}. */
 template <int NV, int K, int LIM, int AXIS, int LANES, bool REC, class Tape>
 __device__ __forceinline__ void field_queue_item(const double* sm, int NP, double* fq, int it, const SchemeDev& S,
                                                  int& st, const Tape& tape, long long lstride) {
