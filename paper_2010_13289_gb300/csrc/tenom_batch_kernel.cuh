@@ -29,9 +29,11 @@ struct BatchTile {
   static constexpr size_t SMEM = sizeof(double) * (PointLayout<3>::NC * NP + NV * TILE);
 };
 
-/* stage: 1 -> out = Us + dt L(Us); 2,3 -> out = cA U0 + cB (Us + dt L(Us)) */
+/* stage: 1 -> out = Us + dt L(Us); 2,3 -> out = cA U0 + cB (Us + dt L(Us)).  Compiled for
+   512 resident threads per SM (128 registers a thread), so that the autotuner's CTA counts
+   can reach 16 warps per SM. */
 template <int K, int LIM, int TILE, bool PP>
-__global__ void __launch_bounds__(TILE)
+__global__ void __launch_bounds__(TILE, 512 / TILE)
 batch_stage_kernel(const BatchArgs A, const double* __restrict__ Us, const double* __restrict__ U0, double* out,
                    int mode, double cA, double cB) {
   using T = BatchTile<K, TILE>;
